@@ -1,0 +1,206 @@
+/*
+ * qoc.h — C ABI of the symmetry-block GRAPE library (libqoc.so).
+ *
+ * Method: Wang, Okyay, Kumar, Wong, "Accelerating Quantum Optimal Control of Multi-Qubit
+ * Systems with Symmetry-Based Hamiltonian Transformations" (arXiv 2309.05884).
+ *   - n qubits, H(t) = H0 + sum_j u_j(t) Hc_j                         (Sec. II.A, Eq. schrodingerEq)
+ *   - piecewise-constant slices, tau = T/N,
+ *     psi_k = exp(-i tau (H0 + sum_j u_kj Hc_j)) psi_{k-1}            (Sec. II.A, Eq. exppropagator)
+ *   - objective F = |<psi_f|psi_N>|^2                                 (Sec. II.A, Eq. probability)
+ *   - the S_n / D_n symmetry makes A^dagger H A block diagonal; every block evolves on its own
+ *                                                                     (Sec. II.A, Fig. 2; Appendix A)
+ *   - gradient of F through the slice derivative of exp and the costates lambda_{k-1} = U_k^dagger
+ *     lambda_k                                                        (Appendix B, Eq. propagator_differentiation)
+ *
+ * Conventions
+ *   - Qubit 1 is the most significant bit of a computational-basis index; |0> = |up>, sigma_z = +1.
+ *   - Complex numbers are interleaved (re, im) doubles.  A "block state" is the concatenation over
+ *     blocks b = 0..n_blocks-1 of c_b copies of an m_b-vector (copy-major: [copy][index]); block b
+ *     starts at complex offset offset_b (see qoc_basis_block).
+ *   - Pulses u are [N][n_ctrl] doubles, row-major; the gradient has the same layout.
+ *   - "dev" = device pointer (CUDA global memory), "host" = host pointer.  The caller owns every
+ *     buffer it passes; the library owns qoc_basis / qoc_plan objects and the device copies of the
+ *     block Hamiltonians they hold.
+ *   - Stream arguments are cudaStream_t passed as void* (NULL = legacy default stream).  Calls that
+ *     take a stream are asynchronous on it; argument errors are returned synchronously before any
+ *     launch.  Kernel-side errors (a NaN pulse, an exhausted iteration cap) are latched in a device
+ *     status word of the plan and returned by qoc_plan_sync_status().
+ *
+ * Every function returns QOC_OK (0) or a negative error code; qoc_last_error() gives a message for
+ * the calling thread's last failure.
+ */
+#ifndef QOC_H
+#define QOC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- error codes */
+enum {
+    QOC_OK = 0,
+    QOC_EINVAL = -1,          /* bad argument, shape, NaN/Inf input, unnormalised state */
+    QOC_ENOMEM = -2,          /* host or device allocation failed, or workspace too small */
+    QOC_ECUDA = -3,           /* a CUDA runtime call failed */
+    QOC_ETIMEOUT = -4,        /* a bounded device wait gave up */
+    QOC_EUNSUPPORTED = -5,    /* a size or option beyond what the library builds */
+    QOC_ENOTCONVERGED = -6    /* optimisation stopped before reaching its target */
+};
+
+/* ---------------------------------------------------------------- Hamiltonian terms */
+/* Operator kinds (coefficient 1); sigma_a^(i) acts on qubit i (Sec. II.A):
+ *   QOC_SUM_a       : sum_i sigma_a^(i)                     (H_x, H_y, H_z of Sec. II.A)
+ *   QOC_ALLPAIRS_aa : sum_{i<j} sigma_a^(i) sigma_a^(j)     (S_n-invariant pair coupling)
+ *   QOC_RING_aa     : sum_{i=1..n} sigma_a^(i) sigma_a^(i+dist), indices mod n
+ *                     (H_{z,cpl} of Sec. II.A for dist = 1; Eq. H0MoreCoupling1 for dist > 1) */
+enum qoc_term_kind {
+    QOC_SUM_X = 0, QOC_SUM_Y = 1, QOC_SUM_Z = 2,
+    QOC_ALLPAIRS_XX = 3, QOC_ALLPAIRS_YY = 4, QOC_ALLPAIRS_ZZ = 5,
+    QOC_RING_XX = 6, QOC_RING_YY = 7, QOC_RING_ZZ = 8
+};
+
+enum { QOC_GROUP_SN = 0, QOC_GROUP_DN = 1 };
+
+typedef struct qoc_term {
+    int kind;      /* enum qoc_term_kind */
+    int dist;      /* ring distance (RING_* only), 1 <= dist <= n/2 */
+    double coeff;  /* real coefficient */
+} qoc_term;
+
+typedef struct qoc_system_desc {
+    int n;                       /* qubits: S_n 1..64, D_n 3..16 */
+    int group;                   /* QOC_GROUP_SN or QOC_GROUP_DN; every term must be invariant */
+    int n_h0_terms;
+    const qoc_term* h0;          /* host, n_h0_terms entries */
+    int n_ctrl;                  /* number of control fields, 1..8 */
+    const int* n_hc_terms;       /* host, n_ctrl entries */
+    const qoc_term* const* hc;   /* host, hc[j] has n_hc_terms[j] entries */
+} qoc_system_desc;
+
+/* ---------------------------------------------------------------- symmetry basis (host, once) */
+typedef struct qoc_basis qoc_basis;
+
+/* Flags for qoc_build_symmetry_basis. */
+enum {
+    QOC_BASIS_FIRST_BLOCK_ONLY = 1,  /* keep only the block of |0...0> (Sec. II.B: H_1 suffices
+                                        when the initial and target states lie in it) */
+    QOC_BASIS_NO_VECTORS = 2         /* do not keep full-space basis vectors (no state conversion) */
+};
+
+/* Build the symmetry-adapted block decomposition of H0 and every Hc_j (Appendix A).
+ * S_n: blocks are the spin sectors J = n/2, n/2-1, ... of size 2J+1 with C(n,n/2-J)-C(n,n/2-J-1)
+ *      identical copies (the |J,M> route of Appendix A); for n > 12 only J = n/2 is built.
+ * D_n: blocks are the irreps A1, A2, (B1, B2), E1, ... of the dihedral group acting on qubit
+ *      indices (Eq. groupAlgebraElementsDn); 2-dimensional irreps have 2 identical copies.
+ * Checks every term's invariance under the group and returns QOC_EINVAL if one is not.
+ * out: receives a basis owned by the library (free with qoc_basis_free).
+ * Errors: QOC_EINVAL (bad desc), QOC_EUNSUPPORTED (n out of range), QOC_ENOMEM. */
+int qoc_build_symmetry_basis(const qoc_system_desc* sys, int flags, qoc_basis** out);
+void qoc_basis_free(qoc_basis* basis);
+
+/* n_blocks, n_ctrl, total block-state length (complex elements), full-space dimension (0 if n>62). */
+int qoc_basis_info(const qoc_basis* basis, int* n_blocks, int* n_ctrl, int64_t* state_len,
+                   int64_t* full_dim);
+
+/* Block b: size m_b, copies c_b, complex offset in the block state, label ("A1", "E2", "J=3/2"...;
+ * label must hold 16 bytes, may be NULL). */
+int qoc_basis_block(const qoc_basis* basis, int b, int* size, int* copies, int64_t* offset,
+                    char* label);
+
+/* Host copies of block b's H0_b (m*m complex) and Hc_jb (n_ctrl*m*m complex), row-major.  Either
+ * pointer may be NULL. */
+int qoc_basis_block_matrices(const qoc_basis* basis, int b, double* h0, double* hc);
+
+/* full (host, 2^n complex) -> blk (host, state_len complex): coordinates <v_{b,r,a}|psi>.
+ * Needs the basis vectors (D_n n <= 16, S_n n <= 12, built without QOC_BASIS_NO_VECTORS). */
+int qoc_state_to_blocks(const qoc_basis* basis, const double* full, double* blk);
+/* blk (host) -> full (host): the inverse map. */
+int qoc_blocks_to_state(const qoc_basis* basis, const double* blk, double* full);
+
+/* The Dicke state |D(n,k)> (k ones, symmetric) in block coordinates (host, state_len complex).
+ * S_n only; it is the basis vector |J=n/2, M=n/2-k> of block 0. */
+int qoc_dicke_state(const qoc_basis* basis, int k, double* blk);
+
+/* ---------------------------------------------------------------- GPU plan */
+typedef struct qoc_plan qoc_plan;
+
+enum {
+    QOC_PREC_F64 = 0,  /* all steps in FP64 */
+    QOC_PREC_F32 = 1   /* complex FP32 Taylor polynomial and sweeps; FP64 squaring chain,
+                          overlap, fidelity and gradient accumulation */
+};
+
+/* Options of a plan; zero-initialise and set what you need (qoc_plan_opts_default fills it). */
+typedef struct qoc_plan_opts {
+    int prec;             /* QOC_PREC_F64 or QOC_PREC_F32 */
+    int grad_mode;        /* 0 = exact slice derivative (Frechet derivative of exp);
+                             1 = the paper's first-order form -i tau Hc_j U_k (Eq. propagator_differentiation) */
+    int max_squarings;    /* cap on the scaling-and-squaring count s (default 16) */
+    int reserved[5];
+} qoc_plan_opts;
+
+void qoc_plan_opts_default(qoc_plan_opts* opts);
+
+/* A plan fixes the basis, the number of slices N, the slice length dt = tau, the options and the
+ * copies that take part.  active (host, one byte per block copy in block-state order, may be NULL
+ * for "all"): copies whose initial or target component is zero cannot contribute to the overlap
+ * and may be left out (Sec. II.B, "only the first block").  Uploads the block Hamiltonians once.
+ * Errors: QOC_EINVAL, QOC_EUNSUPPORTED (a block larger than the kernels support), QOC_ECUDA. */
+int qoc_plan_create(const qoc_basis* basis, int N, double dt, const qoc_plan_opts* opts,
+                    const uint8_t* active, qoc_plan** out);
+void qoc_plan_free(qoc_plan* plan);
+
+/* Bytes of device workspace the plan's calls need (propagators, states and costates, partial
+ * sums).  The caller allocates it (any allocator) and passes it to every call; calls on one plan
+ * and one workspace must not overlap in time. */
+int qoc_plan_workspace_bytes(const qoc_plan* plan, size_t* bytes);
+
+/* Return and clear the plan's device status word (synchronises the given stream). */
+int qoc_plan_sync_status(qoc_plan* plan, void* stream);
+
+/* Block assembly (Eq. exppropagator's exponent): A_out[b][k] = -i dt (H0_b + sum_j u_kj Hc_jb) for
+ * every active block b and slice k, as m_b*m_b complex128 row-major matrices packed block-major
+ * (block b at complex offset N * sum_{b'<b} m_b'^2).
+ * u: dev [N][n_ctrl] doubles.  A_out: dev.  Errors: QOC_EINVAL. */
+int qoc_assemble_blocks(const qoc_plan* plan, const double* u, double* A_out, void* stream);
+
+/* Batched propagators U[b][k] = exp(A[b][k]) by scaling and squaring with a Taylor polynomial
+ * (Sec. II.A, Eq. exppropagator), written as complex128 in the layout of qoc_assemble_blocks. */
+int qoc_expm_blocks(const qoc_plan* plan, const double* u, double* U_out, void* workspace,
+                    size_t workspace_bytes, void* stream);
+
+/* Forward propagation of every active block copy: psiN = U_N ... U_1 psi0 (Eq. exppropagator).
+ * psi0, psiN: dev block states (state_len complex128); inactive copies of psiN are set to 0. */
+int qoc_propagate(const qoc_plan* plan, const double* u, const double* psi0, double* psiN,
+                  void* workspace, size_t workspace_bytes, void* stream);
+
+/* Fidelity and gradient (Eq. probability; Appendix B):
+ *   out3 (dev, 3 doubles) = { F, Re o, Im o },  o = sum over active copies <psif|psi_N>,  F = |o|^2
+ *   grad (dev [N][n_ctrl], may be NULL) = dF/du_kj = 2 Re(conj(o) sum lam_k^dagger dU_k/du_kj psi_{k-1})
+ * psi0, psif: dev block states (state_len complex128). */
+int qoc_fidelity_and_grad(const qoc_plan* plan, const double* u, const double* psi0,
+                          const double* psif, double* out3, double* grad, void* workspace,
+                          size_t workspace_bytes, void* stream);
+
+/* Gradient ascent (GRAPE, Sec. II.A): for it = 0..iters-1: compute F and dF/du, record F in
+ * F_hist[it] (dev, iters doubles), then u <- u + step * dF/du.  u (dev [N][n_ctrl]) is updated
+ * in place.  With f_target <= 1 the loop checks F every check_every iterations on the host and
+ * stops once F >= f_target; *iters_done receives the number of updates made (host, may be NULL).
+ * Returns QOC_ENOTCONVERGED if f_target <= 1 and was not reached. */
+int qoc_optimize_pulses(const qoc_plan* plan, double* u, const double* psi0, const double* psif,
+                        int iters, double step, double f_target, int check_every, double* F_hist,
+                        int* iters_done, void* workspace, size_t workspace_bytes, void* stream);
+
+/* ---------------------------------------------------------------- misc */
+const char* qoc_strerror(int code);
+const char* qoc_last_error(void);
+int qoc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QOC_H */

@@ -1,0 +1,252 @@
+"""Python binding of libqoc (include/qoc.h): Basis, Plan and the autograd wrapper.
+
+Argument marshalling only: every step of the hot path runs in the library's CUDA kernels; torch
+supplies device memory and streams.  Complex device buffers are torch.complex128 tensors (the
+interleaved (re, im) double layout of the C ABI).
+"""
+from __future__ import annotations
+
+import ctypes as C
+from typing import List, Optional, Sequence, Tuple
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+class Basis:
+    """Symmetry-adapted block decomposition of H0 and the Hc_j (Appendix A); built on the host once.
+
+    system: an object with fields n, group, h0 (list of (kind, coeff, dist)), hc (list of such lists)
+    such as paper_2309_05884_gb300.inputs.System."""
+
+    def __init__(self, system, first_block_only: bool = False, vectors: bool = True):
+        self.lib = L.load()
+        self.system = system
+        h0 = (L.qoc_term * max(1, len(system.h0)))(*[L.qoc_term(k, d, c) for k, c, d in system.h0])
+        hcs = [(L.qoc_term * len(t))(*[L.qoc_term(k, d, c) for k, c, d in t]) for t in system.hc]
+        n_hc = (C.c_int * len(hcs))(*[len(t) for t in system.hc])
+        hc_ptrs = (C.POINTER(L.qoc_term) * len(hcs))(*[C.cast(a, C.POINTER(L.qoc_term)) for a in hcs])
+        desc = L.qoc_system_desc(system.n, system.group, len(system.h0), C.cast(h0, C.POINTER(L.qoc_term)),
+                                 len(hcs), C.cast(n_hc, C.POINTER(C.c_int)),
+                                 C.cast(hc_ptrs, C.POINTER(C.POINTER(L.qoc_term))))
+        flags = (L.QOC_BASIS_FIRST_BLOCK_ONLY if first_block_only else 0) | (0 if vectors else L.QOC_BASIS_NO_VECTORS)
+        h = C.c_void_p()
+        L.check(self.lib.qoc_build_symmetry_basis(C.byref(desc), flags, C.byref(h)), "qoc_build_symmetry_basis")
+        self.handle = h
+        nb, nc, sl, fd = C.c_int(), C.c_int(), C.c_int64(), C.c_int64()
+        L.check(self.lib.qoc_basis_info(h, C.byref(nb), C.byref(nc), C.byref(sl), C.byref(fd)), "qoc_basis_info")
+        self.n_blocks, self.n_ctrl, self.state_len, self.full_dim = nb.value, nc.value, sl.value, fd.value
+        self.blocks: List[Tuple[str, int, int, int]] = []
+        for b in range(self.n_blocks):
+            m, c, off = C.c_int(), C.c_int(), C.c_int64()
+            lab = C.create_string_buffer(16)
+            L.check(self.lib.qoc_basis_block(h, b, C.byref(m), C.byref(c), C.byref(off), lab), "qoc_basis_block")
+            self.blocks.append((lab.value.decode(), m.value, c.value, off.value))
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.qoc_basis_free(self.handle)
+            self.handle = None
+
+    @property
+    def n_copies(self) -> int:
+        return sum(c for _, _, c, _ in self.blocks)
+
+    def block_matrices(self, b: int):
+        _, m, _, _ = self.blocks[b]
+        h0 = np.zeros((m, m), np.complex128)
+        hc = np.zeros((self.n_ctrl, m, m), np.complex128)
+        L.check(self.lib.qoc_basis_block_matrices(self.handle, b, h0.ctypes.data_as(C.c_void_p),
+                                                  hc.ctypes.data_as(C.c_void_p)), "qoc_basis_block_matrices")
+        return h0, hc
+
+    def state_to_blocks(self, full: np.ndarray) -> np.ndarray:
+        full = np.ascontiguousarray(full, dtype=np.complex128)
+        assert full.shape == (self.full_dim,)
+        out = np.zeros(self.state_len, np.complex128)
+        L.check(self.lib.qoc_state_to_blocks(self.handle, full.ctypes.data_as(C.c_void_p),
+                                             out.ctypes.data_as(C.c_void_p)), "qoc_state_to_blocks")
+        return out
+
+    def blocks_to_state(self, blk: np.ndarray) -> np.ndarray:
+        blk = np.ascontiguousarray(blk, dtype=np.complex128)
+        out = np.zeros(self.full_dim, np.complex128)
+        L.check(self.lib.qoc_blocks_to_state(self.handle, blk.ctypes.data_as(C.c_void_p),
+                                             out.ctypes.data_as(C.c_void_p)), "qoc_blocks_to_state")
+        return out
+
+    def dicke_state(self, k: int) -> np.ndarray:
+        out = np.zeros(self.state_len, np.complex128)
+        L.check(self.lib.qoc_dicke_state(self.handle, k, out.ctypes.data_as(C.c_void_p)), "qoc_dicke_state")
+        return out
+
+    def copy_norms(self, blk: np.ndarray) -> np.ndarray:
+        """2-norm of every block copy of a block state, in block-state order."""
+        out = []
+        for _, m, c, off in self.blocks:
+            for r in range(c):
+                out.append(np.linalg.norm(blk[off + r * m: off + (r + 1) * m]))
+        return np.array(out)
+
+    def active_copies(self, psi0_blk: np.ndarray, psif_blk: np.ndarray, tol: float = 1e-13) -> np.ndarray:
+        """Copies with support in both states (only those can contribute to <psi_f|psi_N>)."""
+        return ((self.copy_norms(psi0_blk) > tol) & (self.copy_norms(psif_blk) > tol)).astype(np.uint8)
+
+
+class Plan:
+    """A GPU plan: basis, N slices of length dt, precision, and the active block copies."""
+
+    def __init__(self, basis: Basis, N: int, dt: float, prec: str = "f64", grad_mode: int = 0,
+                 active: Optional[np.ndarray] = None, max_squarings: int = 16, device=None):
+        self.lib = L.load()
+        self.basis = basis
+        self.N, self.dt = N, dt
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        opts = L.qoc_plan_opts()
+        self.lib.qoc_plan_opts_default(C.byref(opts))
+        opts.prec = L.QOC_PREC_F64 if prec == "f64" else L.QOC_PREC_F32
+        opts.grad_mode = grad_mode
+        opts.max_squarings = max_squarings
+        self.prec = prec
+        act = None
+        if active is not None:
+            self._active = np.ascontiguousarray(active, dtype=np.uint8)
+            assert self._active.shape == (basis.n_copies,)
+            act = self._active.ctypes.data_as(C.c_void_p)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.qoc_plan_create(basis.handle, N, dt, C.byref(opts), act, C.byref(h)), "qoc_plan_create")
+        self.handle = h
+        nbytes = C.c_size_t()
+        L.check(self.lib.qoc_plan_workspace_bytes(h, C.byref(nbytes)), "qoc_plan_workspace_bytes")
+        self.workspace_bytes = nbytes.value
+        self._ws = None
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.qoc_plan_free(self.handle)
+            self.handle = None
+
+    @property
+    def workspace(self) -> torch.Tensor:
+        if self._ws is None:
+            self._ws = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=self.device)
+        return self._ws
+
+    def release_workspace(self):
+        self._ws = None
+
+    def _check_u(self, u: torch.Tensor):
+        assert u.dtype == torch.float64 and u.is_cuda and u.is_contiguous()
+        assert tuple(u.shape) == (self.N, self.basis.n_ctrl), (tuple(u.shape), (self.N, self.basis.n_ctrl))
+
+    def _check_state(self, s: torch.Tensor):
+        assert s.dtype == torch.complex128 and s.is_cuda and s.is_contiguous()
+        assert s.numel() == self.basis.state_len
+
+    def fidelity_and_grad(self, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, want_grad: bool = True,
+                          out3: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None, stream=None):
+        """(out3 = [F, Re o, Im o], grad [N, nc]) on the device, asynchronously on the stream."""
+        self._check_u(u)
+        self._check_state(psi0)
+        self._check_state(psif)
+        if out3 is None:
+            out3 = torch.empty(3, dtype=torch.float64, device=u.device)
+        if want_grad and grad is None:
+            grad = torch.empty_like(u)
+        ws = self.workspace
+        L.check(self.lib.qoc_fidelity_and_grad(self.handle, _ptr(u), _ptr(psi0), _ptr(psif), _ptr(out3),
+                                               _ptr(grad) if want_grad else None, _ptr(ws), ws.numel(),
+                                               _stream(stream)), "qoc_fidelity_and_grad")
+        return out3, (grad if want_grad else None)
+
+    def propagate(self, u: torch.Tensor, psi0: torch.Tensor, psiN: Optional[torch.Tensor] = None, stream=None):
+        self._check_u(u)
+        self._check_state(psi0)
+        if psiN is None:
+            psiN = torch.empty_like(psi0)
+        ws = self.workspace
+        L.check(self.lib.qoc_propagate(self.handle, _ptr(u), _ptr(psi0), _ptr(psiN), _ptr(ws), ws.numel(),
+                                       _stream(stream)), "qoc_propagate")
+        return psiN
+
+    def assemble(self, u: torch.Tensor, stream=None) -> torch.Tensor:
+        """A[b][k] = -i dt (H0_b + sum_j u_kj Hc_jb), packed block-major over active blocks."""
+        self._check_u(u)
+        out = torch.empty(self.export_elems(), dtype=torch.complex128, device=u.device)
+        L.check(self.lib.qoc_assemble_blocks(self.handle, _ptr(u), _ptr(out), _stream(stream)), "qoc_assemble_blocks")
+        return out
+
+    def expm(self, u: torch.Tensor, stream=None) -> torch.Tensor:
+        """U[b][k] = exp(A[b][k]) in the layout of assemble()."""
+        self._check_u(u)
+        out = torch.empty(self.export_elems(), dtype=torch.complex128, device=u.device)
+        ws = self.workspace
+        L.check(self.lib.qoc_expm_blocks(self.handle, _ptr(u), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
+                "qoc_expm_blocks")
+        return out
+
+    def active_blocks(self) -> List[int]:
+        """Basis indices of blocks with at least one active copy (the export layout's order)."""
+        if getattr(self, "_active", None) is None:
+            return list(range(self.basis.n_blocks))
+        out, i = [], 0
+        for b, (_, m, c, off) in enumerate(self.basis.blocks):
+            if self._active[i:i + c].any():
+                out.append(b)
+            i += c
+        return out
+
+    def export_elems(self) -> int:
+        return sum(self.N * self.basis.blocks[b][1] ** 2 for b in self.active_blocks())
+
+    def optimize(self, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, iters: int, step: float,
+                 f_target: float = 2.0, check_every: int = 10, stream=None):
+        """GRAPE ascent in place on u; returns (F history tensor [iters_done], iterations done, converged)."""
+        self._check_u(u)
+        F_hist = torch.zeros(max(iters, 1), dtype=torch.float64, device=u.device)
+        done = C.c_int(0)
+        ws = self.workspace
+        rc = self.lib.qoc_optimize_pulses(self.handle, _ptr(u), _ptr(psi0), _ptr(psif), iters, step, f_target,
+                                          check_every, _ptr(F_hist), C.byref(done), _ptr(ws), ws.numel(),
+                                          _stream(stream))
+        converged = rc == L.QOC_OK
+        if rc not in (L.QOC_OK, L.QOC_ENOTCONVERGED):
+            L.check(rc, "qoc_optimize_pulses")
+        return F_hist[:done.value], done.value, converged
+
+    def sync_status(self, stream=None) -> None:
+        L.check(self.lib.qoc_plan_sync_status(self.handle, _stream(stream)), "device status")
+
+
+class FidelityGrad(torch.autograd.Function):
+    """F(u) = |<psi_f|psi_N(u)>|^2 with its hand-written adjoint (costate sweep + exact slice
+    derivatives): forward runs the whole hot path once and keeps dF/du for backward."""
+
+    @staticmethod
+    def forward(ctx, u: torch.Tensor, plan: Plan, psi0: torch.Tensor, psif: torch.Tensor):
+        out3, g = plan.fidelity_and_grad(u.detach().contiguous(), psi0, psif, want_grad=True)
+        ctx.save_for_backward(g)
+        return out3[0].clone()
+
+    @staticmethod
+    def backward(ctx, gF):
+        (g,) = ctx.saved_tensors
+        return gF * g, None, None, None
+
+
+def to_device(blk: np.ndarray, device=None) -> torch.Tensor:
+    """A host block state (complex128, length state_len) as a device tensor."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    return torch.from_numpy(np.ascontiguousarray(blk, dtype=np.complex128)).to(dev)

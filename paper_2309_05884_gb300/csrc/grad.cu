@@ -1,0 +1,301 @@
+// Exact slice derivatives of the fidelity (Appendix B) and their reduction to dF/du.
+//
+// For slice k and block b, with A = -i tau (H0_b + sum_j u_kj Hc_jb), E_j = -i tau Hc_jb,
+// psi = psi_{k-1} and lam = lam_k (costate), the Frechet derivative of exp gives
+//     lam^dagger L(A, E_j) psi = sum_{p+q<=P} (A^dagger^p lam)^dagger E_j (A^q psi) / (p+q+1)!
+// (the series L(A,E) = sum_{p,q} A^p E A^q / (p+q+1)!, truncated once beta^{P+1}/(P+1)! is below
+// the tolerance, beta the slice's 1-norm bound).  With v_q = A^q psi, w_p = (A^dagger)^p lam = (-A)^p
+// lam and z_q = sum_{p<=P-q} w_p / (p+q+1)!, the sum is
+//     -i tau sum_{a,b} Hc_j[a][b] * M[a][b],   M[a][b] = sum_q conj(z_q[a]) v_q[b],
+// so every Hc_jb is read once per slice.  The paper's own slice derivative (Eq.
+// propagator_differentiation) is the leading term -i tau Hc_j U_k; grad_mode 1 evaluates it as
+// lam_k^dagger E_j psi_k with the same contraction (one term, z = lam_k, v = psi_k).
+// dF/du_kj = 2 Re(conj(o) * sum_{b, copies} [...]), o = <psi_f|psi_N> (Eq. probability).
+#include "kernels.h"
+
+namespace qoc {
+
+namespace {
+
+constexpr int GRAD_THREADS = 256;
+constexpr int PMAX = 40;
+
+// y = sgn * M x; M m x m row-major (shared or global), x, y in shared memory.  G threads per row.
+template <class T>
+__device__ __forceinline__ void cta_gemv(cx<T>* y, const cx<T>* M, const cx<T>* x, int m, T sgn) {
+    int G = 1;
+    while (G < 32 && G * 2 * m <= (int)blockDim.x) G *= 2;
+    const int outs = blockDim.x / G;
+    const int part = threadIdx.x % G;
+    for (int o0 = 0; o0 < m; o0 += outs) {
+        const int o = o0 + threadIdx.x / G;
+        cx<T> acc = mk<T>(0, 0);
+        if (o < m) {
+            const cx<T>* row = M + (size_t)o * m;
+            for (int j = part; j < m; j += G) cfma<T>(acc, row[j], x[j]);
+        }
+        for (int off = G / 2; off > 0; off >>= 1) {
+            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+        }
+        if (o < m && part == 0) y[o] = mk<T>(sgn * acc.x, sgn * acc.y);
+    }
+    __syncthreads();
+}
+
+template <class T>
+__global__ void __launch_bounds__(GRAD_THREADS)
+grad_kernel(DevPlan P, double tol, double beta_cap, const double* __restrict__ u, const cx<T>* __restrict__ psi_st,
+            const cx<T>* __restrict__ lam_st, double2* __restrict__ partial, char* __restrict__ scratch,
+            size_t slot_bytes, int a_in_smem, int max_m) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ double s_if[PMAX + 2];
+    __shared__ double s_uk[8];
+    __shared__ int s_P;
+    __shared__ double red[GRAD_THREADS / 32][8][2];
+
+    const int N = P.N, nc = P.nc;
+    const long long total = (long long)N * P.nb;
+    // shared layout: [A: max_m^2 if a_in_smem][V: (PMAX+1) max_m][Z: (PMAX+1) max_m][W: 2 max_m]
+    cx<T>* sA = reinterpret_cast<cx<T>*>(dsm);
+    cx<T>* V = sA + (a_in_smem ? (size_t)max_m * max_m : 0);
+    cx<T>* Z = V + (size_t)(PMAX + 1) * max_m;
+    cx<T>* W = Z + (size_t)(PMAX + 1) * max_m;
+    cx<T>* Wn = W + max_m;
+    cx<T>* gA = reinterpret_cast<cx<T>*>(scratch + (size_t)blockIdx.x * slot_bytes);
+    cx<T>* A = a_in_smem ? sA : gA;
+
+    if (threadIdx.x == 0) {
+        double f = 1.0;
+        for (int i = 0; i < PMAX + 2; ++i) { s_if[i] = f; f /= (double)(i + 1); }
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
+        const int bi = (int)(item / N);
+        const int k = (int)(item % N) + 1;  // slice 1..N
+        const DevBlock& B = P.blocks[bi];
+        const int m = B.m, c = B.c;
+        const size_t mm = (size_t)m * m;
+        const T tau = (T)P.dt;
+        if (threadIdx.x == 0) {
+            double beta = B.h0_norm1;
+            for (int j = 0; j < nc; ++j) {
+                const double uk = u[(size_t)(k - 1) * nc + j];
+                s_uk[j] = isfinite(uk) ? uk : 0.0;
+                beta += fabs(s_uk[j]) * B.hc_norm1[j];
+            }
+            beta *= P.dt;
+            int Pt = 0;
+            if (P.grad_mode == 0) {
+                double term = beta;  // beta^{P+1}/(P+1)! at P = 0
+                while (Pt < PMAX && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
+                if (term > tol || beta > beta_cap) atomicOr(P.status, ST_SERIES_CAP);
+            }
+            s_P = Pt;
+        }
+        __syncthreads();
+        const int Pt = s_P;
+        const cx<T>* H = reinterpret_cast<const cx<T>*>(P.H) + B.h_off;
+        if (P.grad_mode == 0) {
+            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                cx<T> h = H[e];
+                for (int j = 0; j < nc; ++j) {
+                    const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                    const T uj = (T)s_uk[j];
+                    h.x = fma(uj, hc.x, h.x);
+                    h.y = fma(uj, hc.y, h.y);
+                }
+                A[e] = cmul_mis<T>(h, tau);
+            }
+        }
+        double accr[8], acci[8];
+        for (int j = 0; j < 8; ++j) accr[j] = acci[j] = 0.0;
+        __syncthreads();
+        for (int r = 0; r < c; ++r) {
+            const cx<T>* psi_prev = psi_st + B.s_off + (long long)(P.grad_mode == 0 ? k - 1 : k) * c * m + (size_t)r * m;
+            const cx<T>* lam_k = lam_st + B.s_off + (long long)k * c * m + (size_t)r * m;
+            for (int a = threadIdx.x; a < m; a += blockDim.x) {
+                V[a] = psi_prev[a];
+                W[a] = lam_k[a];
+            }
+            __syncthreads();
+            for (int q = 1; q <= Pt; ++q) cta_gemv<T>(V + (size_t)q * m, A, V + (size_t)(q - 1) * m, m, (T)1);
+            // z_q = sum_{p <= P-q} w_p / (p+q+1)!, accumulated while the w_p are generated
+            for (int e = threadIdx.x; e < (Pt + 1) * m; e += blockDim.x) Z[e] = mk<T>(0, 0);
+            __syncthreads();
+            for (int p = 0; p <= Pt; ++p) {
+                for (int e = threadIdx.x; e < (Pt - p + 1) * m; e += blockDim.x) {
+                    const int q = e / m, a = e - q * m;
+                    const T cf = (T)s_if[p + q + 1];
+                    Z[e].x = fma(cf, W[a].x, Z[e].x);
+                    Z[e].y = fma(cf, W[a].y, Z[e].y);
+                }
+                __syncthreads();
+                if (p < Pt) {
+                    cta_gemv<T>(Wn, A, W, m, (T)-1);
+                    cx<T>* t = W; W = Wn; Wn = t;
+                }
+            }
+            // contraction with every Hc_j: sum_{a,b} Hc_j[a][b] sum_q conj(Z_q[a]) V_q[b]
+            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                const int a = (int)(e / m), b = (int)(e - (size_t)a * m);
+                cx<T> Mab = mk<T>(0, 0);
+                for (int q = 0; q <= Pt; ++q) cfma_conj<T>(Mab, Z[(size_t)q * m + a], V[(size_t)q * m + b]);
+                for (int j = 0; j < nc; ++j) {
+                    const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                    accr[j] += (double)hc.x * (double)Mab.x - (double)hc.y * (double)Mab.y;
+                    acci[j] += (double)hc.x * (double)Mab.y + (double)hc.y * (double)Mab.x;
+                }
+            }
+            __syncthreads();
+        }
+        // block reduction of the nc complex sums; then multiply by -i tau
+        for (int j = 0; j < nc; ++j) {
+            double xr = accr[j], xi = acci[j];
+            for (int off = 16; off > 0; off >>= 1) {
+                xr += __shfl_xor_sync(0xffffffffu, xr, off);
+                xi += __shfl_xor_sync(0xffffffffu, xi, off);
+            }
+            if (lane == 0) { red[warp][j][0] = xr; red[warp][j][1] = xi; }
+        }
+        __syncthreads();
+        if (threadIdx.x < nc) {
+            double xr = 0.0, xi = 0.0;
+            for (int w = 0; w < GRAD_THREADS / 32; ++w) { xr += red[w][threadIdx.x][0]; xi += red[w][threadIdx.x][1]; }
+            // (-i tau) (xr + i xi) = tau xi - i tau xr
+            double2 o;
+            o.x = P.dt * xi;
+            o.y = -P.dt * xr;
+            partial[((size_t)(k - 1) * P.nb + bi) * nc + threadIdx.x] = o;
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void grad_reduce_kernel(DevPlan P, const double2* __restrict__ partial, const double2* __restrict__ o_ws,
+                                   double* grad, double* u, double step, double* F_hist_slot,
+                                   const double* out3) {
+    const int N = P.N, nc = P.nc;
+    const double2 o = *o_ws;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N * nc; e += gridDim.x * blockDim.x) {
+        const int k = e / nc, j = e - k * nc;
+        double sr = 0.0, si = 0.0;
+        for (int bi = 0; bi < P.nb; ++bi) {
+            const double2 d = partial[((size_t)k * P.nb + bi) * nc + j];
+            sr += d.x;
+            si += d.y;
+        }
+        // 2 Re(conj(o) * s)
+        const double g = 2.0 * (o.x * sr + o.y * si);
+        if (grad) grad[e] = g;
+        if (u && step != 0.0) u[e] += step * g;
+    }
+    if (F_hist_slot && blockIdx.x == 0 && threadIdx.x == 0) *F_hist_slot = out3[0];
+}
+
+__global__ void assemble_kernel(DevPlan P, const double* __restrict__ u, const double2* __restrict__ H64,
+                                double2* __restrict__ A_out, const long long* __restrict__ a_off) {
+    const int bi = blockIdx.y;
+    const DevBlock& B = P.blocks[bi];
+    const int m = B.m;
+    const size_t mm = (size_t)m * m;
+    const double2* H = H64 + B.h_off;
+    for (int k = blockIdx.x; k < P.N; k += gridDim.x) {
+        for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+            double2 h = H[e];
+            for (int j = 0; j < P.nc; ++j) {
+                const double uj = u[(size_t)k * P.nc + j];
+                const double2 hc = H[(size_t)(1 + j) * mm + e];
+                h.x = fma(uj, hc.x, h.x);
+                h.y = fma(uj, hc.y, h.y);
+            }
+            double2 a;
+            a.x = P.dt * h.y;
+            a.y = -P.dt * h.x;
+            A_out[a_off[bi] + (size_t)k * mm + e] = a;
+        }
+    }
+}
+
+template <class T>
+size_t grad_smem(int max_m, int a_in_smem) {
+    return (a_in_smem ? (size_t)max_m * max_m : 0) * sizeof(cx<T>) +
+           (size_t)(2 * (PMAX + 1) + 2) * max_m * sizeof(cx<T>);
+}
+
+constexpr size_t GRAD_SMEM_LIMIT = 200 * 1024;
+
+template <class T>
+int a_fits(int max_m) {
+    return grad_smem<T>(max_m, 1) <= GRAD_SMEM_LIMIT;
+}
+
+}  // namespace
+
+size_t grad_slot_bytes(int prec, int max_m) {
+    const int fits = prec == 0 ? a_fits<double>(max_m) : a_fits<float>(max_m);
+    if (fits) return 0;
+    return (size_t)max_m * max_m * (prec == 0 ? 16 : 8) + 256;
+}
+
+int grad_grid_limit(int prec, int max_m) {
+    int dev = 0, sms = 0, occ = 1;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (prec == 0) {
+        const int fits = a_fits<double>(max_m);
+        const size_t sm = grad_smem<double>(max_m, fits);
+        cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grad_kernel<double>, GRAD_THREADS, sm);
+    } else {
+        const int fits = a_fits<float>(max_m);
+        const size_t sm = grad_smem<float>(max_m, fits);
+        cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grad_kernel<float>, GRAD_THREADS, sm);
+    }
+    if (occ < 1) occ = 1;
+    return sms * occ;
+}
+
+int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store,
+                         double2* partial, char* scratch, size_t slot_bytes, int max_m, int grid,
+                         cudaStream_t st) {
+    if (P.nc > 8) return -2;
+    if (P.prec == 0) {
+        const int fits = a_fits<double>(max_m);
+        const size_t sm = grad_smem<double>(max_m, fits);
+        if (sm > 220 * 1024) return -2;
+        cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grad_kernel<double><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-17, 8.0, u, (const double2*)psi_store,
+                                                           (const double2*)lam_store, partial, scratch, slot_bytes,
+                                                           fits, max_m);
+    } else {
+        const int fits = a_fits<float>(max_m);
+        const size_t sm = grad_smem<float>(max_m, fits);
+        if (sm > 220 * 1024) return -2;
+        cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-9, 4.0, u, (const float2*)psi_store,
+                                                          (const float2*)lam_store, partial, scratch, slot_bytes,
+                                                          fits, max_m);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_grad_reduce(const DevPlan& P, const double2* partial, const double2* o_ws, double* grad, double* u,
+                       double step, double* F_hist_slot, const double* out3, cudaStream_t st) {
+    const int n = P.N * P.nc;
+    int blocks = (n + 255) / 256;
+    if (blocks > 1024) blocks = 1024;
+    if (blocks < 1) blocks = 1;
+    grad_reduce_kernel<<<blocks, 256, 0, st>>>(P, partial, o_ws, grad, u, step, F_hist_slot, out3);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_assemble(const DevPlan& P, const double* u, double2* A_out, const long long* a_off, cudaStream_t st) {
+    dim3 grid(P.N < 1024 ? P.N : 1024, P.nb);
+    assemble_kernel<<<grid, 256, 0, st>>>(P, u, P.H64, A_out, a_off);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+}  // namespace qoc

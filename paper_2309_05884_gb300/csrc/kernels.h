@@ -1,0 +1,53 @@
+// Launch wrappers of the CUDA kernels (host-callable, no templates in the interface).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+namespace qoc {
+
+// Degree table of the Taylor / Paterson-Stockmeyer scheme: theta[i] is the largest 1-norm bound
+// for which degree (p_i q_i) keeps the truncation below the working unit roundoff.
+struct ExpmTables {
+    double theta[9];
+    int n_deg;          // degrees allowed (prefix of the table)
+    double theta_cap;   // largest norm the polynomial is evaluated at; larger norms are scaled
+};
+
+// ---- expm.cu
+size_t expm_slot_bytes(int prec, int m_max);
+int expm_r_for(int prec, int m);
+int expm_grid_limit(int prec, int R);
+int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls, int R,
+                void* Uout, char* scratch, size_t slot_bytes, int m_max, int grid, cudaStream_t st);
+// U_out[a_off[b] + k*m*m + e] (complex128, unpadded) <- the working-precision propagators.
+int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st);
+
+// ---- sweep.cu
+// Forward (psi_k = U_k psi_{k-1}) and/or backward (lam_{k-1} = U_k^dagger lam_k) sweeps of every
+// active block, one CTA per (direction, block).  dirs: 1 = forward, 2 = backward, 3 = both.
+int launch_sweeps(const DevPlan& P, const void* U, const double2* psi0, const double2* psif, void* psi_store,
+                  void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st);
+// o = sum_{active copies} <psif | psi_N>  (FP64), out3 = {|o|^2, Re o, Im o}; o also stored in o_ws.
+int launch_overlap(const DevPlan& P, const void* psi_store, const double2* psif, double* out3, double2* o_ws,
+                   cudaStream_t st);
+// psiN (caller's block state, complex128) <- psi_N of every active copy; the rest is zeroed.
+int launch_store_final(const DevPlan& P, const void* psi_store, double2* psiN, long long state_len,
+                       cudaStream_t st);
+
+// ---- grad.cu
+// Per-slice, per-block partial derivatives do[k][b][j] = sum_r lam_k^dagger dU_k/du_kj psi_{k-1}.
+int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store,
+                         double2* partial, char* scratch, size_t slot_bytes, int max_m, int grid,
+                         cudaStream_t st);
+size_t grad_slot_bytes(int prec, int max_m);
+int grad_grid_limit(int prec, int max_m);
+// grad[k][j] = 2 Re(conj(o) sum_b do[k][b][j]); if step != 0 also u[k][j] += step * grad[k][j].
+int launch_grad_reduce(const DevPlan& P, const double2* partial, const double2* o_ws, double* grad, double* u,
+                       double step, double* F_hist_slot, const double* out3, cudaStream_t st);
+// A_out[b][k] = -i dt (H0_b + sum_j u_kj Hc_jb) in complex128.
+int launch_assemble(const DevPlan& P, const double* u, double2* A_out, const long long* a_off, cudaStream_t st);
+
+}  // namespace qoc
