@@ -1,0 +1,314 @@
+"""Benchmark: GRAPE gradient evaluations per second on the D_10 XXZ ring workload.
+
+Workload (default): n = 10 qubits, H0 = sum_i (X_i X_{i+1} + Y_i Y_{i+1} + 0.5 Z_i Z_{i+1}) on a
+periodic ring, controls u_x sum X, u_y sum Y, u_z sum Z, T = 20, N = 500 slices, pulses ~ N(0, 0.3^2)
+(seed 1).  All eight D_10 irrep blocks (A1 78, A2 30, B1 58, B2 42, E1 99 x2, E2 105 x2, E3 99 x2,
+E4 105 x2) carry amplitude: the initial and target states are seeded random full-space states, so
+every block is propagated.  Complex FP32 Taylor polynomial and sweeps, FP64 squaring chain, overlap
+and gradient accumulation.  One step = one GRAPE iteration: F, dF/du (exact slice derivatives) and
+the update u <- u + eps dF/du, all on the device.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of the same
+workload (the first 50 slices per step, scaled to whole gradient evaluations).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2309_05884_gb300 import inputs as I  # noqa: E402
+
+METRIC = "GRAPE grad evals/s"
+UNIT = "grad_evals/s"
+WORKLOAD = ("D_10 XXZ ring (n=10, T=20, N=500, 3 controls), all 8 D_10 irrep blocks active "
+            "(A1 78, A2 30, B1 58, B2 42, E1-E4 99/105 x2 copies)")
+EPS = 0.5          # GRAPE step
+SEED_U, SEED_PSI0, SEED_PSIF = 1, 101, 102
+FP32_PEAK_NOTE = "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max SM clock) = 80.5 TFLOP/s"
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def workload():
+    s = I.c2_system()
+    psi0 = I.random_state(SEED_PSI0, 2 ** s.n)
+    psif = I.random_state(SEED_PSIF, 2 ** s.n)
+    u = I.pulses_normal(SEED_U, s.N, s.n_ctrl)
+    return s, psi0, psif, u
+
+
+# --------------------------------------------------------------------------- clocks
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 10:
+                continue
+            try:
+                rows.append(dict(sm=float(f[1]), smax=float(f[2]), power=float(f[3]),
+                                 hw=f[5], hwt=f[6], swt=f[7], pcap=f[8], util=float(f[9])))
+            except ValueError:
+                continue
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        loaded = [r for r in rows if r["util"] > 0] or rows
+        reasons = set()
+        for r in loaded:
+            if r["hw"].startswith("Active"):
+                reasons.add("hw_slowdown")
+            if r["hwt"].startswith("Active"):
+                reasons.add("hw_thermal_slowdown")
+            if r["swt"].startswith("Active"):
+                reasons.add("sw_thermal_slowdown")
+            if r["pcap"].startswith("Active"):
+                reasons.add("sw_power_cap")
+        return {"sm_mhz": float(np.median([r["sm"] for r in loaded])), "sm_max_mhz": loaded[0]["smax"],
+                "power_w_max": max(r["power"] for r in loaded), "reasons": sorted(reasons),
+                "samples": len(loaded)}
+
+
+# --------------------------------------------------------------------------- oracle (CPU) legs
+def oracle_problem(s, psi0, psif, N_sample):
+    from oracle import operators as op
+    from oracle import symmetry as sy
+    sub = I.System(s.n, s.group, s.h0, s.hc, s.tau * N_sample, N_sample)
+    H0, Hc = op.system_operators(sub)
+    return sub, sy.block_problem(sub, H0, Hc, sy.symmetry_blocks(sub), psi0, psif)
+
+
+def cpu_oracle_rate(s, psi0, psif, u, N_sample, reps=1):
+    """Grad evals/s of the oracle on the first N_sample slices, scaled to the whole workload."""
+    from oracle import grape as gr
+    sub, prob = oracle_problem(s, psi0, psif, N_sample)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        gr.fidelity_and_grad(prob, u[:N_sample], sub.tau)
+    dt = time.perf_counter() - t0
+    return reps * (N_sample / s.N) / dt, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    s, psi0, psif, u = workload()
+    from oracle import grape as gr
+    Ns = 50
+    sub, prob = oracle_problem(s, psi0, psif, Ns)
+    uu = u[:Ns].copy()
+    for _ in range(args.warmup):
+        _, _, g = gr.fidelity_and_grad(prob, uu, sub.tau)
+        uu += EPS * g
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, _, g = gr.fidelity_and_grad(prob, uu, sub.tau)
+        uu += EPS * g
+    dt = time.perf_counter() - t0
+    value = args.steps * (Ns / s.N) / dt
+    cores = os.cpu_count()
+    sample = (f"each step: oracle F + exact gradient + update on the first {Ns} of {s.N} slices "
+              f"(all blocks), scaled by {Ns}/{s.N}")
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# --------------------------------------------------------------------------- GPU leg
+def run_ours(args, rank, world):
+    import torch
+    from paper_2309_05884_gb300 import api
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    s, psi0_full, psif_full, u0 = workload()
+    B = api.Basis(s)
+    b0, bf = B.state_to_blocks(psi0_full), B.state_to_blocks(psif_full)
+    plan = api.Plan(B, s.N, s.tau, prec="f32", active=B.active_copies(b0, bf))
+    d0, df = api.to_device(b0, dev), api.to_device(bf, dev)
+    u = torch.from_numpy(u0.copy()).to(dev)
+    ws = plan.workspace  # allocate before timing
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+
+    def step():
+        plan.optimize(u, d0, df, iters=1, step=EPS)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.sync_status()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    # timed region: K steps, each bracketed by events on the launching stream, L2 flushed between
+    plan.set_profiling(True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    phases = []
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            flush.zero_()
+            evs[i][0].record(stream)
+            step()
+            evs[i][1].record(stream)
+            phases.append(plan.phase_times())
+        torch.cuda.synchronize()
+        barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    counts = plan.work_counts()
+    plan.set_profiling(False)
+    plan.sync_status()
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * args.steps / (total_ms / 1e3)
+    ph = np.mean(np.array(phases), axis=0)
+
+    # roofline of the dominant kernel (the batched expm): algorithmic flops per launch set
+    flops_poly = 8.0 * counts[0] / args.steps       # complex MAC = 8 real flops
+    flops_sq = 8.0 * counts[1] / args.steps
+    expm_ms = float(ph[0])
+    achieved = (flops_poly + flops_sq) / (expm_ms * 1e-3) / 1e12
+    roof = {"bound": "alu", "kernel": "expm_kernel (all size classes of one call)",
+            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+            "traffic": None, "peak_source": FP32_PEAK_NOTE,
+            "flops_per_launch": flops_poly + flops_sq, "fp64_squaring_flops": flops_sq,
+            "phase_ms": {"expm": float(ph[0]), "sweeps": float(ph[1]), "overlap": float(ph[2]),
+                         "slice_derivatives": float(ph[3]), "reduce_update": float(ph[4])}}
+
+    # end to end through the C ABI with host buffers: H2D of u and both states, D2H of F and dF/du
+    u_h = torch.from_numpy(u0.copy()).pin_memory()
+    b0_h = torch.from_numpy(b0).pin_memory()
+    bf_h = torch.from_numpy(bf).pin_memory()
+    out_h = torch.empty(3, dtype=torch.float64).pin_memory()
+    g_h = torch.empty_like(u_h).pin_memory()
+    u_d, d0e, dfe = torch.empty_like(u), torch.empty_like(d0), torch.empty_like(df)
+    out3 = torch.empty(3, dtype=torch.float64, device=dev)
+    gd = torch.empty_like(u)
+    e2e_steps = max(3, args.steps // 2)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        u_d.copy_(u_h, non_blocking=True)
+        d0e.copy_(b0_h, non_blocking=True)
+        dfe.copy_(bf_h, non_blocking=True)
+        plan.fidelity_and_grad(u_d, d0e, dfe, out3=out3, grad=gd)
+        out_h.copy_(out3, non_blocking=True)
+        g_h.copy_(gd, non_blocking=True)
+        torch.cuda.synchronize()
+        u_h += EPS * g_h
+    e2e_s = time.perf_counter() - t0
+    h2d = u_h.numel() * 8 + b0_h.numel() * 16 + bf_h.numel() * 16
+    d2h = 3 * 8 + g_h.numel() * 8
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ns = 250
+        rate, secs = cpu_oracle_rate(s, psi0_full, psif_full, u0, Ns)
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"one FP64 oracle F + exact gradient over the first {Ns} of {s.N} slices "
+                         f"(all blocks, numpy/BLAS default threads), {secs:.1f} s, scaled by {Ns}/{s.N}"}
+
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "precision": "complex FP32 polynomial + sweeps; FP64 squaring, "
+                                                          "overlap, gradient accumulation",
+                       "problems_per_step": 1, "l2": "flushed between timed steps (256 MB write)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": plan.kernel_launches(True) * args.steps,
+            "clocks": clk.summary(),
+        }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world)
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

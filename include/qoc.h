@@ -194,6 +194,20 @@ int qoc_optimize_pulses(const qoc_plan* plan, double* u, const double* psi0, con
                         int iters, double step, double f_target, int check_every, double* F_hist,
                         int* iters_done, void* workspace, size_t workspace_bytes, void* stream);
 
+/* ---------------------------------------------------------------- measurement */
+/* Phase timing: when enabled, every later call records CUDA events on its stream between its
+ * phases.  qoc_plan_phase_times waits for the last call and writes up to n_out durations in ms:
+ *   [0] assembly + batched expm, [1] forward/backward sweeps, [2] overlap, [3] slice derivatives,
+ *   [4] gradient reduction / update.
+ * Work counters (reset by enabling): counts[0] = sum over (slice, block) items of m^3 times the
+ * polynomial products taken (working precision), counts[1] = sum of m^3 times the FP64 squarings,
+ * counts[2] = (slice, block) items exponentiated. */
+int qoc_plan_set_profiling(qoc_plan* plan, int on);
+int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
+int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);
+/* Number of kernel launches one qoc_fidelity_and_grad (with_grad = 1) or qoc_propagate (0) call makes. */
+int qoc_plan_kernel_launches(const qoc_plan* plan, int with_grad, int* launches);
+
 /* ---------------------------------------------------------------- misc */
 const char* qoc_strerror(int code);
 const char* qoc_last_error(void);

@@ -65,6 +65,10 @@ SIGNATURES = {
     "qoc_fidelity_and_grad": (C.c_int, [P, P, P, P, P, P, P, C.c_size_t, P]),
     "qoc_optimize_pulses": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_int, P,
                                       C.POINTER(C.c_int), P, C.c_size_t, P]),
+    "qoc_plan_set_profiling": (C.c_int, [P, C.c_int]),
+    "qoc_plan_phase_times": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
+    "qoc_plan_work_counts": (C.c_int, [P, C.POINTER(C.c_longlong), C.c_int]),
+    "qoc_plan_kernel_launches": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
     "qoc_strerror": (C.c_char_p, [C.c_int]),
     "qoc_last_error": (C.c_char_p, []),
     "qoc_version": (C.c_int, []),

@@ -226,6 +226,26 @@ class Plan:
             L.check(rc, "qoc_optimize_pulses")
         return F_hist[:done.value], done.value, converged
 
+    def set_profiling(self, on: bool = True) -> None:
+        L.check(self.lib.qoc_plan_set_profiling(self.handle, int(on)), "qoc_plan_set_profiling")
+
+    def phase_times(self) -> List[float]:
+        """[expm, sweeps, overlap, slice derivatives, reduction] of the last call, in ms."""
+        ms = (C.c_float * 5)()
+        L.check(self.lib.qoc_plan_phase_times(self.handle, ms, 5), "qoc_plan_phase_times")
+        return list(ms)
+
+    def work_counts(self) -> List[int]:
+        """[sum m^3 * polynomial products, sum m^3 * FP64 squarings, items] since profiling was enabled."""
+        out = (C.c_longlong * 3)()
+        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 3), "qoc_plan_work_counts")
+        return list(out)
+
+    def kernel_launches(self, with_grad: bool = True) -> int:
+        n = C.c_int()
+        L.check(self.lib.qoc_plan_kernel_launches(self.handle, int(with_grad), C.byref(n)), "qoc_plan_kernel_launches")
+        return n.value
+
     def sync_status(self, stream=None) -> None:
         L.check(self.lib.qoc_plan_sync_status(self.handle, _stream(stream)), "device status")
 

@@ -74,6 +74,7 @@ struct DevPlan {
     const void* H;             // packed block Hamiltonians in the working precision
     const double2* H64;        // the same in FP64
     int* status;
+    unsigned long long* stats;  // work counters or null
 };
 
 }  // namespace qoc

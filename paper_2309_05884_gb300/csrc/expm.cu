@@ -80,6 +80,12 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
             s_p = c_deg_p[di];
             s_q = c_deg_q[di];
             s_scale = P.dt / (double)(1LL << s);
+            if (P.stats) {
+                const unsigned long long m3 = (unsigned long long)m * m * m;
+                atomicAdd(P.stats + 0, m3 * (unsigned long long)(c_deg_p[di] + c_deg_q[di] - 2));
+                atomicAdd(P.stats + 1, m3 * (unsigned long long)s);
+                atomicAdd(P.stats + 2, 1ull);
+            }
         }
         __syncthreads();
         const int s = s_sq, p = s_p, q = s_q;

@@ -49,6 +49,9 @@ struct qoc_plan {
     double2* d_H64 = nullptr;
     int* d_cls = nullptr;
     int* d_status = nullptr;
+    unsigned long long* d_stats = nullptr;
+    bool profiling = false;
+    cudaEvent_t ev[6] = {};
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
            off_grad = 0;
@@ -69,6 +72,7 @@ struct qoc_plan {
         P.H = d_H;
         P.H64 = d_H64;
         P.status = d_status;
+        P.stats = profiling ? d_stats : nullptr;
         (void)ws;
         return P;
     }
@@ -286,6 +290,10 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
     if ((e = cudaMalloc(&p->d_H64, sizeof(cplx) * H64.size())) != cudaSuccess) return fail(e, "cudaMalloc H");
     if ((e = cudaMalloc(&p->d_cls, sizeof(int) * std::max<size_t>(1, cls_list.size()))) != cudaSuccess) return fail(e, "cudaMalloc classes");
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc status");
+    if ((e = cudaMalloc(&p->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc stats");
+    cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
+    for (auto& ev : p->ev)
+        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e, "cudaEventCreate");
     cudaMemcpy(p->d_blocks, p->hblocks.data(), sizeof(DevBlock) * p->nb, cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_copy_src, p->copy_src.data(), sizeof(int64_t) * p->copy_src.size(), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_copy_base, p->copy_base.data(), sizeof(int64_t) * p->nb, cudaMemcpyHostToDevice);
@@ -319,6 +327,9 @@ void qoc_plan_free(qoc_plan* p) {
     cudaFree(p->d_H64);
     cudaFree(p->d_cls);
     cudaFree(p->d_status);
+    cudaFree(p->d_stats);
+    for (auto& ev : p->ev)
+        if (ev) cudaEventDestroy(ev);
     delete p;
 }
 
@@ -341,6 +352,47 @@ int qoc_plan_sync_status(qoc_plan* p, void* stream) {
     if (st & ST_NAN_PULSE) return set_error(QOC_EINVAL, "non-finite pulse value");
     if (st & ST_SQUARING_CAP) return set_error(QOC_EUNSUPPORTED, "a slice needed more squarings than max_squarings");
     if (st & ST_SERIES_CAP) return set_error(QOC_EUNSUPPORTED, "a slice's norm is beyond the gradient series' range");
+    return QOC_OK;
+}
+
+int qoc_plan_set_profiling(qoc_plan* p, int on) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    cudaSetDevice(p->device);
+    p->profiling = on != 0;
+    if (on) cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
+    return QOC_OK;
+}
+
+int qoc_plan_phase_times(qoc_plan* p, float* ms, int n) {
+    if (!p || !ms) return set_error(QOC_EINVAL, "null argument");
+    if (!p->profiling) return set_error(QOC_EINVAL, "profiling is off");
+    cudaSetDevice(p->device);
+    cudaError_t e = cudaEventSynchronize(p->ev[5]);
+    if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
+    for (int i = 0; i < n && i < 5; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "event elapsed");
+        ms[i] = t;
+    }
+    return QOC_OK;
+}
+
+int qoc_plan_work_counts(qoc_plan* p, long long* out, int n) {
+    if (!p || !out) return set_error(QOC_EINVAL, "null argument");
+    cudaSetDevice(p->device);
+    unsigned long long h[4] = {0, 0, 0, 0};
+    cudaError_t e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "stats read");
+    for (int i = 0; i < n && i < 3; ++i) out[i] = (long long)h[i];
+    return QOC_OK;
+}
+
+int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
+    if (!p || !launches) return set_error(QOC_EINVAL, "null argument");
+    // expm: one launch per size class; then sweeps, overlap, slice derivatives, reduction
+    // (propagate: sweeps and the final-state store after a memset)
+    *launches = (int)p->classes.size() + (with_grad ? 4 : 2);
     return QOC_OK;
 }
 
@@ -386,20 +438,31 @@ static int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* 
                               cudaStream_t st) {
     int rc;
     const DevPlan P = p->dev(w);
+    auto mark = [&](int i) {
+        if (p->profiling) cudaEventRecord(p->ev[i], st);
+    };
+    mark(0);
     if ((rc = run_expm(p, u, w, st))) return rc;
+    mark(1);
     if ((rc = run_sweeps(p, psi0, psif, grad || u_update ? 3 : 1, w, st))) return rc;
+    mark(2);
     double2* o_ws = reinterpret_cast<double2*>(w + p->off_o);
     if (launch_overlap(P, w + p->off_psi, reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
         return cuda_fail(cudaGetLastError(), "overlap launch");
+    mark(3);
     if (grad || u_update) {
         const int g = launch_grad_partials(P, u, w + p->off_psi, w + p->off_lam, reinterpret_cast<double2*>(w + p->off_partial),
                                            w + p->off_grad, p->grad_slot, p->max_m, p->grad_grid, st);
         if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
         if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
+        mark(4);
         if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial), o_ws, grad, u_update, step,
                                F_slot, out3, st) != 0)
             return cuda_fail(cudaGetLastError(), "reduce launch");
+    } else {
+        mark(4);
     }
+    mark(5);
     return QOC_OK;
 }
 
