@@ -208,6 +208,24 @@ int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);
 /* Number of kernel launches one qoc_fidelity_and_grad (with_grad = 1) or qoc_propagate (0) call makes. */
 int qoc_plan_kernel_launches(const qoc_plan* plan, int with_grad, int* launches);
 
+/* ---------------------------------------------------------------- allocation-free variant */
+/* The paper has no counterpart to this entry point; it serves callers that cannot allocate device
+ * memory while they run (a real-time loop that forbids allocator calls after start-up, a host whose
+ * device memory is owned by another runtime, a caller without an allocator for a plan workspace).
+ *
+ * U[i] = exp(A[i]) for count complex FP64 m x m matrices (dev, row-major, interleaved re/im, A and
+ * U of count*m*m complex each; U must not overlap A), by scaling and squaring with a Taylor
+ * polynomial in FP64 (the method of qoc_expm_blocks, applied to arbitrary matrices).  Allocates
+ * nothing: its working matrices live in a 16 MiB array inside the loaded library, which every GPU
+ * that loads libqoc.so keeps until the process exits.
+ *   - m must be 1..128, else QOC_EUNSUPPORTED with a message; count >= 0 (0 is a no-op).
+ *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ *     that device current; make that first call before any stream capture starts.
+ *   - All calls share the array: calls whose kernels overlap on the GPU (other streams, other host
+ *     threads) race and return wrong results; serialise them.
+ *   - Asynchronous on 'stream'; errors of the launch itself are returned. */
+int qoc_expm_batch_noalloc(const double* A, double* U, int m, long long count, void* stream);
+
 /* ---------------------------------------------------------------- misc */
 const char* qoc_strerror(int code);
 const char* qoc_last_error(void);

@@ -69,6 +69,7 @@ SIGNATURES = {
     "qoc_plan_phase_times": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
     "qoc_plan_work_counts": (C.c_int, [P, C.POINTER(C.c_longlong), C.c_int]),
     "qoc_plan_kernel_launches": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
+    "qoc_expm_batch_noalloc": (C.c_int, [P, P, C.c_int, C.c_longlong, P]),
     "qoc_strerror": (C.c_char_p, [C.c_int]),
     "qoc_last_error": (C.c_char_p, []),
     "qoc_version": (C.c_int, []),
