@@ -139,7 +139,12 @@ typedef struct qoc_plan_opts {
     int grad_mode;        /* 0 = exact slice derivative (Frechet derivative of exp);
                              1 = the paper's first-order form -i tau Hc_j U_k (Eq. propagator_differentiation) */
     int max_squarings;    /* cap on the scaling-and-squaring count s (default 16) */
-    int reserved[5];
+    int ckpt_segment;     /* 0 = keep every propagator of a call in the workspace (default);
+                             S > 0 = checkpointing: keep the state at every S-th slice and only S
+                             slices of propagators; the costate pass recomputes each segment's
+                             propagators and states (twice the exponentials, workspace ~ N/S + S
+                             states and S propagators per block); -1 = S = ceil(sqrt(N)) */
+    int reserved[4];
 } qoc_plan_opts;
 
 void qoc_plan_opts_default(qoc_plan_opts* opts);

@@ -37,7 +37,7 @@ class qoc_system_desc(C.Structure):
 
 class qoc_plan_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("grad_mode", C.c_int), ("max_squarings", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("ckpt_segment", C.c_int), ("reserved", C.c_int * 4)]
 
 
 # name -> (restype, argtypes); every symbol include/qoc.h declares

@@ -108,7 +108,8 @@ class Plan:
     """A GPU plan: basis, N slices of length dt, precision, and the active block copies."""
 
     def __init__(self, basis: Basis, N: int, dt: float, prec: str = "f64", grad_mode: int = 0,
-                 active: Optional[np.ndarray] = None, max_squarings: int = 16, device=None):
+                 active: Optional[np.ndarray] = None, max_squarings: int = 16, ckpt_segment: int = 0,
+                 device=None):
         self.lib = L.load()
         self.basis = basis
         self.N, self.dt = N, dt
@@ -118,6 +119,7 @@ class Plan:
         opts.prec = L.QOC_PREC_F64 if prec == "f64" else L.QOC_PREC_F32
         opts.grad_mode = grad_mode
         opts.max_squarings = max_squarings
+        opts.ckpt_segment = ckpt_segment
         self.prec = prec
         act = None
         if active is not None:

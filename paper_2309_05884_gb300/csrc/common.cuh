@@ -54,7 +54,8 @@ struct DevBlock {
     int64_t mmp;      // padded stride (elements) between consecutive U_b[k]: m*m rounded up to 4
     int64_t h_off;    // complex offset of H0_b in the packed Hamiltonian array; Hc_jb at h_off + (1+j)*m*m
     int64_t u_off;    // complex offset of U_b[k=0] in the propagator area (U_b[k] at u_off + k*mmp)
-    int64_t s_off;    // complex offset of psi_b[k=0] in the state areas (psi_b[k] at s_off + k*c*m)
+    int64_t s_off;    // complex offset of psi_b[slot 0] in the window state areas (slot i at s_off + i*c*m)
+    int64_t v_off;    // complex offset of block b in a boundary-vector array [b][copy][m]
     double h0_norm1;  // max column 1-norm of H0_b
     double hc_norm1[8];
 };
@@ -62,6 +63,8 @@ struct DevBlock {
 // Everything a kernel needs about the plan, passed by value.
 struct DevPlan {
     int N;            // slices
+    int k0;           // first slice (0-based) of the current window
+    int nk;           // slices in the current window
     int nc;           // controls
     int nb;           // active blocks
     int prec;         // QOC_PREC_*

@@ -35,8 +35,8 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     __shared__ double s_scale;
     __shared__ int s_sq, s_p, s_q;
 
-    const int N = P.N;
-    const long long total = (long long)n_cls * N;
+    const int NK = P.nk;
+    const long long total = (long long)n_cls * NK;
     char* slot = scratch + (size_t)blockIdx.x * slot_bytes;
     const size_t mm_max = (size_t)m_max * m_max;
     cx<T>* base = reinterpret_cast<cx<T>*>(slot);
@@ -53,8 +53,9 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     if (threadIdx.x < 8) pw[threadIdx.x] = base + (size_t)(threadIdx.x < 6 ? threadIdx.x : 0) * mm_max;
 
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        const int bi = cls_blocks[item / N];
-        const int k = (int)(item % N);
+        const int bi = cls_blocks[item / NK];
+        const int kw = (int)(item % NK);  // slot in the window
+        const int k = P.k0 + kw;          // slice (0-based)
         const DevBlock& B = P.blocks[bi];
         const int m = B.m;
         const size_t mm = (size_t)m * m;
@@ -142,7 +143,7 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
         }
 
         // s squarings in FP64, then store in the working precision
-        cx<T>* Uo = reinterpret_cast<cx<T>*>(Uout) + B.u_off + (size_t)k * B.mmp;
+        cx<T>* Uo = reinterpret_cast<cx<T>*>(Uout) + B.u_off + (size_t)kw * B.mmp;
         if (s == 0) {
             for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
         } else {
@@ -173,15 +174,15 @@ __global__ void export_u_kernel(DevPlan P, const cx<T>* __restrict__ U, double2*
     const int bi = blockIdx.y;
     const DevBlock& B = P.blocks[bi];
     const size_t mm = (size_t)B.m * B.m;
-    for (int k = blockIdx.x; k < P.N; k += gridDim.x)
+    for (int k = blockIdx.x; k < P.nk; k += gridDim.x)
         for (size_t e = threadIdx.x; e < mm; e += blockDim.x)
-            out[a_off[bi] + (size_t)k * mm + e] = ccast<double, T>(U[B.u_off + (size_t)k * B.mmp + e]);
+            out[a_off[bi] + (size_t)(P.k0 + k) * mm + e] = ccast<double, T>(U[B.u_off + (size_t)k * B.mmp + e]);
 }
 
 }  // namespace
 
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st) {
-    dim3 grid(P.N < 1024 ? P.N : 1024, P.nb);
+    dim3 grid(P.nk < 1024 ? P.nk : 1024, P.nb);
     if (P.prec == 0)
         export_u_kernel<double><<<grid, 256, 0, st>>>(P, (const double2*)U, U_out, a_off);
     else

@@ -17,63 +17,84 @@ namespace qoc {
 
 namespace {
 
-constexpr int GRAD_THREADS = 256;
-constexpr int PMAX = 40;
+constexpr int GRAD_THREADS = 512;
+// P: longest series; CG: copies processed together (2*CG right-hand sides per pass over A)
+template <class T> struct GradCfg;
+template <> struct GradCfg<float> { static constexpr int P = 24, CG = 2; };
+template <> struct GradCfg<double> { static constexpr int P = 40, CG = 1; };
 
-// y = sgn * M x; M m x m row-major (shared or global), x, y in shared memory.  G threads per row.
-template <class T>
-__device__ __forceinline__ void cta_gemv(cx<T>* y, const cx<T>* M, const cx<T>* x, int m, T sgn) {
+// ys[v] = sgn[v] * M xs[v] for v < nv (nv <= NV); M is m x m row-major (shared or global), the
+// vectors are in shared memory.  G threads share a row; M[o][j] is read once for all nv vectors.
+template <class T, int NV>
+__device__ __forceinline__ void cta_gemv_multi(cx<T>* const* ys, const cx<T>* M, const cx<T>* const* xs,
+                                               const T* sgn, int nv, int m) {
     int G = 1;
     while (G < 32 && G * 2 * m <= (int)blockDim.x) G *= 2;
     const int outs = blockDim.x / G;
     const int part = threadIdx.x % G;
     for (int o0 = 0; o0 < m; o0 += outs) {
         const int o = o0 + threadIdx.x / G;
-        cx<T> acc = mk<T>(0, 0);
+        cx<T> acc[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) acc[v] = mk<T>(0, 0);
         if (o < m) {
             const cx<T>* row = M + (size_t)o * m;
-            for (int j = part; j < m; j += G) cfma<T>(acc, row[j], x[j]);
+            for (int j = part; j < m; j += G) {
+                const cx<T> a = row[j];
+#pragma unroll
+                for (int v = 0; v < NV; ++v)
+                    if (v < nv) cfma<T>(acc[v], a, xs[v][j]);
+            }
         }
-        for (int off = G / 2; off > 0; off >>= 1) {
-            acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
-            acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+            if (v >= nv) break;
+            for (int off = G / 2; off > 0; off >>= 1) {
+                acc[v].x += __shfl_xor_sync(0xffffffffu, acc[v].x, off);
+                acc[v].y += __shfl_xor_sync(0xffffffffu, acc[v].y, off);
+            }
+            if (o < m && part == 0) ys[v][o] = mk<T>(sgn[v] * acc[v].x, sgn[v] * acc[v].y);
         }
-        if (o < m && part == 0) y[o] = mk<T>(sgn * acc.x, sgn * acc.y);
     }
     __syncthreads();
 }
 
+// Shared layout (elements of cx<T>): [A: m^2 if a_in_smem][V: (PM+1)*CG*m][Z: (PM+1)*CG*m][W: CG*m][Wn: CG*m]
 template <class T>
 __global__ void __launch_bounds__(GRAD_THREADS)
 grad_kernel(DevPlan P, double tol, double beta_cap, const double* __restrict__ u, const cx<T>* __restrict__ psi_st,
             const cx<T>* __restrict__ lam_st, double2* __restrict__ partial, char* __restrict__ scratch,
             size_t slot_bytes, int a_in_smem, int max_m) {
+    constexpr int PM = GradCfg<T>::P;
+    constexpr int CG = GradCfg<T>::CG;
     extern __shared__ __align__(16) unsigned char dsm[];
-    __shared__ double s_if[PMAX + 2];
+    __shared__ double s_if[PM + 2];
     __shared__ double s_uk[8];
     __shared__ int s_P;
     __shared__ double red[GRAD_THREADS / 32][8][2];
 
-    const int N = P.N, nc = P.nc;
-    const long long total = (long long)N * P.nb;
-    // shared layout: [A: max_m^2 if a_in_smem][V: (PMAX+1) max_m][Z: (PMAX+1) max_m][W: 2 max_m]
-    cx<T>* sA = reinterpret_cast<cx<T>*>(dsm);
-    cx<T>* V = sA + (a_in_smem ? (size_t)max_m * max_m : 0);
-    cx<T>* Z = V + (size_t)(PMAX + 1) * max_m;
-    cx<T>* W = Z + (size_t)(PMAX + 1) * max_m;
-    cx<T>* Wn = W + max_m;
+    const int NK = P.nk, nc = P.nc;
+    const long long total = (long long)NK * P.nb;
+    // a_in_smem: 1 = A and the vector families in shared memory; 0 = A in this CTA's global slot,
+    // vectors in shared memory; -1 = both in the global slot (large blocks)
     cx<T>* gA = reinterpret_cast<cx<T>*>(scratch + (size_t)blockIdx.x * slot_bytes);
-    cx<T>* A = a_in_smem ? sA : gA;
+    cx<T>* sA = reinterpret_cast<cx<T>*>(dsm);
+    cx<T>* A = a_in_smem == 1 ? sA : gA;
+    cx<T>* V = a_in_smem == 1 ? sA + (size_t)max_m * max_m : a_in_smem == 0 ? sA : gA + (size_t)max_m * max_m;
+    cx<T>* Z = V + (size_t)(PM + 1) * CG * max_m;
+    cx<T>* W = Z + (size_t)(PM + 1) * CG * max_m;
+    cx<T>* Wn = W + (size_t)CG * max_m;
 
     if (threadIdx.x == 0) {
         double f = 1.0;
-        for (int i = 0; i < PMAX + 2; ++i) { s_if[i] = f; f /= (double)(i + 1); }
+        for (int i = 0; i < PM + 2; ++i) { s_if[i] = f; f /= (double)(i + 1); }
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        const int bi = (int)(item / N);
-        const int k = (int)(item % N) + 1;  // slice 1..N
+        const int bi = (int)(item / NK);
+        const int kw = (int)(item % NK);   // window slot: psi_{k-1} in slot kw, lam_k in slot kw+1
+        const int k = P.k0 + kw + 1;       // slice 1..N
         const DevBlock& B = P.blocks[bi];
         const int m = B.m, c = B.c;
         const size_t mm = (size_t)m * m;
@@ -89,7 +110,7 @@ grad_kernel(DevPlan P, double tol, double beta_cap, const double* __restrict__ u
             int Pt = 0;
             if (P.grad_mode == 0) {
                 double term = beta;  // beta^{P+1}/(P+1)! at P = 0
-                while (Pt < PMAX && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
+                while (Pt < PM && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
                 if (term > tol || beta > beta_cap) atomicOr(P.status, ST_SERIES_CAP);
             }
             s_P = Pt;
@@ -109,50 +130,89 @@ grad_kernel(DevPlan P, double tol, double beta_cap, const double* __restrict__ u
                 A[e] = cmul_mis<T>(h, tau);
             }
         }
-        double accr[8], acci[8];
-        for (int j = 0; j < 8; ++j) accr[j] = acci[j] = 0.0;
+        // per-thread partial sums in the working precision (a thread adds ~m^2/blockDim terms);
+        // the cross-thread reduction below is FP64
+        T accr[8], acci[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) accr[j] = acci[j] = (T)0;
         __syncthreads();
-        for (int r = 0; r < c; ++r) {
-            const cx<T>* psi_prev = psi_st + B.s_off + (long long)(P.grad_mode == 0 ? k - 1 : k) * c * m + (size_t)r * m;
-            const cx<T>* lam_k = lam_st + B.s_off + (long long)k * c * m + (size_t)r * m;
-            for (int a = threadIdx.x; a < m; a += blockDim.x) {
-                V[a] = psi_prev[a];
-                W[a] = lam_k[a];
+        for (int r0 = 0; r0 < c; r0 += CG) {
+            const int cg = (c - r0) < CG ? (c - r0) : CG;
+            // V[q][r] at V + (q*CG + r)*m ; Z likewise ; W[r] at W + r*m
+            const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
+            for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
+                const int r = e / m, a = e - r * m;
+                V[(size_t)r * m + a] = psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a];
+                W[(size_t)r * m + a] = lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a];
             }
-            __syncthreads();
-            for (int q = 1; q <= Pt; ++q) cta_gemv<T>(V + (size_t)q * m, A, V + (size_t)(q - 1) * m, m, (T)1);
-            // z_q = sum_{p <= P-q} w_p / (p+q+1)!, accumulated while the w_p are generated
-            for (int e = threadIdx.x; e < (Pt + 1) * m; e += blockDim.x) Z[e] = mk<T>(0, 0);
+            for (int e = threadIdx.x; e < (Pt + 1) * CG * m; e += blockDim.x) Z[e] = mk<T>(0, 0);
             __syncthreads();
             for (int p = 0; p <= Pt; ++p) {
-                for (int e = threadIdx.x; e < (Pt - p + 1) * m; e += blockDim.x) {
-                    const int q = e / m, a = e - q * m;
+                // z_q += w_p / (p+q+1)!  for q <= P-p
+                for (int e = threadIdx.x; e < (Pt - p + 1) * cg * m; e += blockDim.x) {
+                    const int q = e / (cg * m);
+                    const int ra = e - q * cg * m;
                     const T cf = (T)s_if[p + q + 1];
-                    Z[e].x = fma(cf, W[a].x, Z[e].x);
-                    Z[e].y = fma(cf, W[a].y, Z[e].y);
+                    cx<T>& z = Z[(size_t)q * CG * m + ra];
+                    const cx<T> w = W[ra];
+                    z.x = fma(cf, w.x, z.x);
+                    z.y = fma(cf, w.y, z.y);
                 }
                 __syncthreads();
                 if (p < Pt) {
-                    cta_gemv<T>(Wn, A, W, m, (T)-1);
+                    // one pass over A: v_{p+1} = A v_p and w_{p+1} = -A w_p for every copy of the group
+                    cx<T>* ys[2 * CG];
+                    const cx<T>* xs[2 * CG];
+                    T sg[2 * CG];
+#pragma unroll
+                    for (int r = 0; r < CG; ++r) {
+                        // v vectors in slots [0, cg), w vectors in [cg, 2cg); unused slots are never read
+                        const int rr = r < cg ? r : 0;
+                        xs[r] = V + ((size_t)p * CG + rr) * m;
+                        ys[r] = V + ((size_t)(p + 1) * CG + rr) * m;
+                        sg[r] = (T)1;
+                    }
+#pragma unroll
+                    for (int r = 0; r < CG; ++r) {
+                        const int rr = r < cg ? r : 0;
+                        xs[CG + r] = W + (size_t)rr * m;
+                        ys[CG + r] = Wn + (size_t)rr * m;
+                        sg[CG + r] = (T)-1;
+                    }
+                    if (cg < CG) {  // pack the w vectors right after the v vectors
+                        for (int r = 0; r < cg; ++r) {
+                            xs[cg + r] = xs[CG + r];
+                            ys[cg + r] = ys[CG + r];
+                            sg[cg + r] = (T)-1;
+                        }
+                    }
+                    cta_gemv_multi<T, 2 * CG>(ys, A, xs, sg, 2 * cg, m);
                     cx<T>* t = W; W = Wn; Wn = t;
                 }
             }
-            // contraction with every Hc_j: sum_{a,b} Hc_j[a][b] sum_q conj(Z_q[a]) V_q[b]
+            // contraction with every Hc_j: sum_{a,b} Hc_j[a][b] sum_{q,r} conj(Z_qr[a]) V_qr[b]
             for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
                 const int a = (int)(e / m), b = (int)(e - (size_t)a * m);
                 cx<T> Mab = mk<T>(0, 0);
-                for (int q = 0; q <= Pt; ++q) cfma_conj<T>(Mab, Z[(size_t)q * m + a], V[(size_t)q * m + b]);
-                for (int j = 0; j < nc; ++j) {
-                    const cx<T> hc = H[(size_t)(1 + j) * mm + e];
-                    accr[j] += (double)hc.x * (double)Mab.x - (double)hc.y * (double)Mab.y;
-                    acci[j] += (double)hc.x * (double)Mab.y + (double)hc.y * (double)Mab.x;
+                for (int q = 0; q <= Pt; ++q)
+                    for (int r = 0; r < cg; ++r)
+                        cfma_conj<T>(Mab, Z[((size_t)q * CG + r) * m + a], V[((size_t)q * CG + r) * m + b]);
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j < nc) {
+                        const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                        accr[j] = fma(hc.x, Mab.x, fma(-hc.y, Mab.y, accr[j]));
+                        acci[j] = fma(hc.x, Mab.y, fma(hc.y, Mab.x, acci[j]));
+                    }
                 }
             }
             __syncthreads();
         }
         // block reduction of the nc complex sums; then multiply by -i tau
-        for (int j = 0; j < nc; ++j) {
-            double xr = accr[j], xi = acci[j];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            if (j >= nc) break;
+            double xr = (double)accr[j], xi = (double)acci[j];
             for (int off = 16; off > 0; off >>= 1) {
                 xr += __shfl_xor_sync(0xffffffffu, xr, off);
                 xi += __shfl_xor_sync(0xffffffffu, xi, off);
@@ -219,38 +279,57 @@ __global__ void assemble_kernel(DevPlan P, const double* __restrict__ u, const d
 }
 
 template <class T>
-size_t grad_smem(int max_m, int a_in_smem) {
-    return (a_in_smem ? (size_t)max_m * max_m : 0) * sizeof(cx<T>) +
-           (size_t)(2 * (PMAX + 1) + 2) * max_m * sizeof(cx<T>);
+size_t grad_vec_elems(int max_m) {
+    return (size_t)(2 * (GradCfg<T>::P + 1) * GradCfg<T>::CG + 2 * GradCfg<T>::CG) * max_m;
 }
 
-constexpr size_t GRAD_SMEM_LIMIT = 200 * 1024;
+// placement mode (see grad_kernel): 1, 0 or -1
+template <class T>
+int grad_mode_of(int max_m) {
+    const size_t limit = 220 * 1024;
+    const size_t vec = grad_vec_elems<T>(max_m) * sizeof(cx<T>);
+    const size_t a = (size_t)max_m * max_m * sizeof(cx<T>);
+    if (vec + a <= limit) return 1;
+    if (vec <= limit) return 0;
+    return -1;
+}
 
 template <class T>
-int a_fits(int max_m) {
-    return grad_smem<T>(max_m, 1) <= GRAD_SMEM_LIMIT;
+size_t grad_smem(int max_m) {
+    const int md = grad_mode_of<T>(max_m);
+    if (md == 1) return ((size_t)max_m * max_m + grad_vec_elems<T>(max_m)) * sizeof(cx<T>);
+    if (md == 0) return grad_vec_elems<T>(max_m) * sizeof(cx<T>);
+    return 0;
+}
+
+template <class T>
+size_t grad_slot(int max_m) {
+    const int md = grad_mode_of<T>(max_m);
+    if (md == 1) return 0;
+    size_t e = (size_t)max_m * max_m + (md == -1 ? grad_vec_elems<T>(max_m) : 0);
+    return e * sizeof(cx<T>) + 256;
 }
 
 }  // namespace
 
-size_t grad_slot_bytes(int prec, int max_m) {
-    const int fits = prec == 0 ? a_fits<double>(max_m) : a_fits<float>(max_m);
-    if (fits) return 0;
-    return (size_t)max_m * max_m * (prec == 0 ? 16 : 8) + 256;
+size_t grad_vector_smem(int prec, int max_m) {
+    (void)prec;
+    (void)max_m;
+    return 0;  // the vector families fall back to global memory when they do not fit
 }
+
+size_t grad_slot_bytes(int prec, int max_m) { return prec == 0 ? grad_slot<double>(max_m) : grad_slot<float>(max_m); }
 
 int grad_grid_limit(int prec, int max_m) {
     int dev = 0, sms = 0, occ = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (prec == 0) {
-        const int fits = a_fits<double>(max_m);
-        const size_t sm = grad_smem<double>(max_m, fits);
+        const size_t sm = grad_smem<double>(max_m);
         cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grad_kernel<double>, GRAD_THREADS, sm);
     } else {
-        const int fits = a_fits<float>(max_m);
-        const size_t sm = grad_smem<float>(max_m, fits);
+        const size_t sm = grad_smem<float>(max_m);
         cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, grad_kernel<float>, GRAD_THREADS, sm);
     }
@@ -263,21 +342,17 @@ int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_stor
                          cudaStream_t st) {
     if (P.nc > 8) return -2;
     if (P.prec == 0) {
-        const int fits = a_fits<double>(max_m);
-        const size_t sm = grad_smem<double>(max_m, fits);
-        if (sm > 220 * 1024) return -2;
+        const size_t sm = grad_smem<double>(max_m);
         cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<double><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-17, 8.0, u, (const double2*)psi_store,
                                                            (const double2*)lam_store, partial, scratch, slot_bytes,
-                                                           fits, max_m);
+                                                           grad_mode_of<double>(max_m), max_m);
     } else {
-        const int fits = a_fits<float>(max_m);
-        const size_t sm = grad_smem<float>(max_m, fits);
-        if (sm > 220 * 1024) return -2;
+        const size_t sm = grad_smem<float>(max_m);
         cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-9, 4.0, u, (const float2*)psi_store,
                                                           (const float2*)lam_store, partial, scratch, slot_bytes,
-                                                          fits, max_m);
+                                                          grad_mode_of<float>(max_m), max_m);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

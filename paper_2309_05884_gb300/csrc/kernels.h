@@ -26,16 +26,18 @@ int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st);
 
 // ---- sweep.cu
-// Forward (psi_k = U_k psi_{k-1}) and/or backward (lam_{k-1} = U_k^dagger lam_k) sweeps of every
-// active block, one CTA per (direction, block).  dirs: 1 = forward, 2 = backward, 3 = both.
-int launch_sweeps(const DevPlan& P, const void* U, const double2* psi0, const double2* psif, void* psi_store,
-                  void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st);
-// o = sum_{active copies} <psif | psi_N>  (FP64), out3 = {|o|^2, Re o, Im o}; o also stored in o_ws.
-int launch_overlap(const DevPlan& P, const void* psi_store, const double2* psif, double* out3, double2* o_ws,
+// Forward (psi_{i+1} = U_i psi_i) and/or backward (lam_i = U_i^dagger lam_{i+1}) sweeps over the
+// current slice window of every active block, one CTA per (direction, block); dirs: 1 = forward,
+// 2 = backward, 3 = both.  Boundary vectors are [block][copy][m] arrays in the working precision.
+int launch_sweeps(const DevPlan& P, const void* U, const void* fwd_init, void* fwd_out, const void* bwd_init,
+                  void* bwd_out, void* psi_store, void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st);
+// dst (boundary layout, working precision) <- the caller's block state (complex128).
+int launch_gather(const DevPlan& P, const double2* src, void* dst, cudaStream_t st);
+// o = sum_{active copies} <psif | psi_N> (FP64) with psi_N in boundary layout; out3 = {|o|^2, Re o, Im o}.
+int launch_overlap(const DevPlan& P, const void* fin, const double2* psif, double* out3, double2* o_ws,
                    cudaStream_t st);
-// psiN (caller's block state, complex128) <- psi_N of every active copy; the rest is zeroed.
-int launch_store_final(const DevPlan& P, const void* psi_store, double2* psiN, long long state_len,
-                       cudaStream_t st);
+// psiN (caller's block state, complex128) <- fin (boundary layout); inactive copies are zeroed.
+int launch_store_final(const DevPlan& P, const void* fin, double2* psiN, long long state_len, cudaStream_t st);
 
 // ---- grad.cu
 // Per-slice, per-block partial derivatives do[k][b][j] = sum_r lam_k^dagger dU_k/du_kj psi_{k-1}.
@@ -43,6 +45,8 @@ int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_stor
                          double2* partial, char* scratch, size_t slot_bytes, int max_m, int grid,
                          cudaStream_t st);
 size_t grad_slot_bytes(int prec, int max_m);
+// Shared memory the slice-derivative kernel needs for its vector families (without A).
+size_t grad_vector_smem(int prec, int max_m);
 int grad_grid_limit(int prec, int max_m);
 // grad[k][j] = 2 Re(conj(o) sum_b do[k][b][j]); if step != 0 also u[k][j] += step * grad[k][j].
 int launch_grad_reduce(const DevPlan& P, const double2* partial, const double2* o_ws, double* grad, double* u,

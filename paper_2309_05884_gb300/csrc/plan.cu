@@ -40,6 +40,9 @@ struct qoc_plan {
     std::vector<ExpmClass> classes;
     int grad_grid = 0;
     size_t grad_slot = 0;
+    int seg = 0;                    // slices per checkpoint segment (== N without checkpointing)
+    int nseg = 1;                   // segments
+    int64_t vlen = 0;               // complex elements of one boundary vector set (sum c*m)
     // device
     DevBlock* d_blocks = nullptr;
     int64_t* d_copy_src = nullptr;
@@ -54,12 +57,15 @@ struct qoc_plan {
     cudaEvent_t ev[6] = {};
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
-           off_grad = 0;
+           off_grad = 0, off_ckpt = 0, off_lamb = 0;
+    size_t el = 16;
     size_t ws_bytes = 0;
 
-    DevPlan dev(char* ws) const {
+    DevPlan dev(char* ws, int k0 = 0, int nk = -1) const {
         DevPlan P{};
         P.N = N;
+        P.k0 = k0;
+        P.nk = nk < 0 ? N : nk;
         P.nc = nc;
         P.nb = nb;
         P.prec = opts.prec;
@@ -112,8 +118,8 @@ int check_ws(const qoc_plan* p, void* ws, size_t bytes) {
     return QOC_OK;
 }
 
-int run_expm(const qoc_plan* p, const double* u, char* ws, cudaStream_t st) {
-    const DevPlan P = p->dev(ws);
+int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
+    const DevPlan P = p->dev(ws, k0, nk);
     for (const auto& c : p->classes) {
         if (launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, c.R, ws + p->off_U, ws + p->off_expm,
                         c.slot_bytes, c.m_max, c.grid, st) != 0)
@@ -122,13 +128,40 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, cudaStream_t st) {
     return QOC_OK;
 }
 
-int run_sweeps(const qoc_plan* p, const double* psi0, const double* psif, int dirs, char* ws, cudaStream_t st) {
-    const DevPlan P = p->dev(ws);
-    const int rc = launch_sweeps(P, ws + p->off_U, reinterpret_cast<const double2*>(psi0),
-                                 reinterpret_cast<const double2*>(psif), ws + p->off_psi, ws + p->off_lam, dirs,
-                                 p->max_m, p->max_c, st);
+char* ckpt_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_ckpt + (size_t)i * p->vlen * p->el; }
+char* lamb_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_lamb + (size_t)i * p->vlen * p->el; }
+
+int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char* fwd_in, char* fwd_out,
+               const char* bwd_in, char* bwd_out, cudaStream_t st) {
+    const DevPlan P = p->dev(ws, k0, nk);
+    const int rc = launch_sweeps(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
+                                 ws + p->off_lam, dirs, p->max_m, p->max_c, st);
     if (rc == -2) return set_error(QOC_EUNSUPPORTED, "block states do not fit in shared memory");
     if (rc != 0) return cuda_fail(cudaGetLastError(), "sweep launch");
+    return QOC_OK;
+}
+
+int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
+    const DevPlan P = p->dev(ws, k0, nk);
+    const int g = launch_grad_partials(P, u, ws + p->off_psi, ws + p->off_lam,
+                                       reinterpret_cast<double2*>(ws + p->off_partial), ws + p->off_grad,
+                                       p->grad_slot, p->max_m, p->grad_grid, st);
+    if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
+    if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
+    return QOC_OK;
+}
+
+// Forward pass over all segments: psi_0 (gathered into checkpoint 0) -> checkpoint nseg = psi_N.
+int forward_pass(const qoc_plan* p, const double* u, const double* psi0, char* w, cudaStream_t st) {
+    int rc;
+    if (launch_gather(p->dev(w), reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0)
+        return cuda_fail(cudaGetLastError(), "gather launch");
+    for (int s = 0; s < p->nseg; ++s) {
+        const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
+        if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
+        if ((rc = run_sweeps(p, w, k0, nk, 1, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), nullptr, nullptr, st)))
+            return rc;
+    }
     return QOC_OK;
 }
 
@@ -167,6 +200,15 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
     p->nc = B->n_ctrl;
     cudaGetDevice(&p->device);
     const size_t el = o.prec == QOC_PREC_F64 ? 16 : 8;
+    p->el = el;
+    if (o.ckpt_segment < -1) {
+        delete p;
+        return set_error(QOC_EINVAL, "ckpt_segment must be -1, 0 or positive");
+    }
+    p->seg = o.ckpt_segment == 0 ? N
+             : o.ckpt_segment < 0 ? std::max(1, (int)std::ceil(std::sqrt((double)N)))
+                                  : std::min(o.ckpt_segment, N);
+    p->nseg = (N + p->seg - 1) / p->seg;
 
     // active blocks, ordered by size (largest first) for load balance
     struct Act { int b; std::vector<int> copies; };
@@ -187,7 +229,7 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
                      [&](const Act& x, const Act& y) { return B->blocks[x.b].m > B->blocks[y.b].m; });
     p->nb = (int)acts.size();
 
-    int64_t h_off = 0, u_off = 0, s_off = 0;
+    int64_t h_off = 0, u_off = 0, s_off = 0, v_off = 0;
     std::vector<cplx> H64;
     for (const auto& a : acts) {
         const auto& blk = B->blocks[a.b];
@@ -199,6 +241,7 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
         d.h_off = h_off;
         d.u_off = u_off;
         d.s_off = s_off;
+        d.v_off = v_off;
         d.h0_norm1 = blk.h0_norm1;
         for (int j = 0; j < p->nc; ++j) d.hc_norm1[j] = blk.hc_norm1[j];
         p->copy_base.push_back((int64_t)p->copy_src.size());
@@ -206,8 +249,9 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
         H64.insert(H64.end(), blk.h0.begin(), blk.h0.end());
         H64.insert(H64.end(), blk.hc.begin(), blk.hc.end());
         h_off += (int64_t)(1 + p->nc) * blk.m * blk.m;
-        u_off += (int64_t)N * d.mmp;
-        s_off += (int64_t)(N + 1) * d.c * d.m;
+        u_off += (int64_t)p->seg * d.mmp;
+        s_off += (int64_t)(p->seg + 1) * d.c * d.m;
+        v_off += (int64_t)d.c * d.m;
         p->max_m = std::max(p->max_m, d.m);
         p->max_c = std::max(p->max_c, d.c);
         p->hblocks.push_back(d);
@@ -250,7 +294,7 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
                 c.m_max = std::max(c.m_max, p->hblocks[i].m);
             }
         if (c.count == 0) continue;
-        const long long items = (long long)c.count * N;
+        const long long items = (long long)c.count * p->seg;
         c.grid = (int)std::min<long long>(items, expm_grid_limit(o.prec, R));
         c.slot_bytes = align_up(expm_slot_bytes(o.prec, c.m_max), 256);
         expm_scratch = std::max(expm_scratch, c.slot_bytes * (size_t)c.grid);
@@ -258,8 +302,9 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
     }
     // gradient kernel
     p->grad_slot = align_up(grad_slot_bytes(o.prec, p->max_m), 256);
-    p->grad_grid = (int)std::min<long long>((long long)N * p->nb, grad_grid_limit(o.prec, p->max_m));
-    if ((size_t)(2 * 41 + 2) * p->max_m * el > 220 * 1024) {
+    p->grad_grid = (int)std::min<long long>((long long)p->seg * p->nb, grad_grid_limit(o.prec, p->max_m));
+    p->vlen = v_off;
+    if (grad_vector_smem(o.prec, p->max_m) > 220 * 1024) {
         delete p;
         return set_error(QOC_EUNSUPPORTED, "block too large for the gradient kernel's shared-memory series");
     }
@@ -274,6 +319,8 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
     p->off_out3 = off;    off = align_up(off + 32, 256);
     p->off_expm = off;    off = align_up(off + expm_scratch, 256);
     p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
+    p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
+    p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
     p->ws_bytes = off;
 
     // device uploads
@@ -392,7 +439,12 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     if (!p || !launches) return set_error(QOC_EINVAL, "null argument");
     // expm: one launch per size class; then sweeps, overlap, slice derivatives, reduction
     // (propagate: sweeps and the final-state store after a memset)
-    *launches = (int)p->classes.size() + (with_grad ? 4 : 2);
+    const int ncls = (int)p->classes.size();
+    if (p->nseg == 1)
+        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + 1 : 1 + ncls + 1 + 1;  // gathers, expm, sweeps, overlap, grad, reduce
+    else
+        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (ncls + 2) + 1
+                              : 1 + p->nseg * (ncls + 1) + 1;
     return QOC_OK;
 }
 
@@ -411,10 +463,13 @@ int qoc_expm_blocks(const qoc_plan* p, const double* u, double* U_out, void* ws,
     if (rc) return rc;
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
-    rc = run_expm(p, u, w, to_stream(stream));
-    if (rc) return rc;
-    if (launch_export_u(p->dev(w), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, to_stream(stream)) != 0)
-        return cuda_fail(cudaGetLastError(), "export launch");
+    cudaStream_t st = to_stream(stream);
+    for (int s = 0; s < p->nseg; ++s) {
+        const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
+        if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
+        if (launch_export_u(p->dev(w, k0, nk), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
+            return cuda_fail(cudaGetLastError(), "export launch");
+    }
     return QOC_OK;
 }
 
@@ -426,13 +481,16 @@ int qoc_propagate(const qoc_plan* p, const double* u, const double* psi0, double
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
-    if ((rc = run_expm(p, u, w, st))) return rc;
-    if ((rc = run_sweeps(p, psi0, psi0, 1, w, st))) return rc;
-    if (launch_store_final(p->dev(w), w + p->off_psi, reinterpret_cast<double2*>(psiN), p->basis->state_len, st) != 0)
+    if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
+    if (launch_store_final(p->dev(w), ckpt_vec(p, w, p->nseg), reinterpret_cast<double2*>(psiN), p->basis->state_len,
+                           st) != 0)
         return cuda_fail(cudaGetLastError(), "store launch");
     return QOC_OK;
 }
 
+// Phase events: [0]..[1] propagators (+ forward sweeps when checkpointing), [1]..[2] sweeps (costate
+// pass when checkpointing: recomputed propagators, both sweeps and slice derivatives), [2]..[3]
+// overlap, [3]..[4] slice derivatives (0 when checkpointing), [4]..[5] reduction / update.
 static int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif,
                               double* out3, double* grad, double* u_update, double step, double* F_slot, char* w,
                               cudaStream_t st) {
@@ -441,26 +499,51 @@ static int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* 
     auto mark = [&](int i) {
         if (p->profiling) cudaEventRecord(p->ev[i], st);
     };
-    mark(0);
-    if ((rc = run_expm(p, u, w, st))) return rc;
-    mark(1);
-    if ((rc = run_sweeps(p, psi0, psif, grad || u_update ? 3 : 1, w, st))) return rc;
-    mark(2);
+    const bool want_grad = grad || u_update;
     double2* o_ws = reinterpret_cast<double2*>(w + p->off_o);
-    if (launch_overlap(P, w + p->off_psi, reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
-        return cuda_fail(cudaGetLastError(), "overlap launch");
-    mark(3);
-    if (grad || u_update) {
-        const int g = launch_grad_partials(P, u, w + p->off_psi, w + p->off_lam, reinterpret_cast<double2*>(w + p->off_partial),
-                                           w + p->off_grad, p->grad_slot, p->max_m, p->grad_grid, st);
-        if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
-        if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
-        mark(4);
+    mark(0);
+    if (p->nseg == 1) {
+        if (launch_gather(P, reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0 ||
+            (want_grad && launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0))
+            return cuda_fail(cudaGetLastError(), "gather launch");
+        if ((rc = run_expm(p, u, w, 0, p->N, st))) return rc;
+        mark(1);
+        if ((rc = run_sweeps(p, w, 0, p->N, want_grad ? 3 : 1, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1),
+                             lamb_vec(p, w, 0), lamb_vec(p, w, 1), st)))
+            return rc;
+        mark(2);
+        if (launch_overlap(P, ckpt_vec(p, w, 1), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+            return cuda_fail(cudaGetLastError(), "overlap launch");
+        mark(3);
+        if (want_grad && (rc = run_grad(p, u, w, 0, p->N, st))) return rc;
+    } else {
+        if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
+        mark(1);
+        if (launch_overlap(P, ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+            return cuda_fail(cudaGetLastError(), "overlap launch");
+        mark(2);
+        if (want_grad) {
+            if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
+                return cuda_fail(cudaGetLastError(), "gather launch");
+            // costate pass: recompute each segment's propagators and states, newest segment first
+            int cur = 0;
+            for (int s = p->nseg - 1; s >= 0; --s) {
+                const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
+                if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
+                if ((rc = run_sweeps(p, w, k0, nk, 3, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), lamb_vec(p, w, cur),
+                                     lamb_vec(p, w, cur ^ 1), st)))
+                    return rc;
+                if ((rc = run_grad(p, u, w, k0, nk, st))) return rc;
+                cur ^= 1;
+            }
+        }
+        mark(3);
+    }
+    mark(4);
+    if (want_grad) {
         if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial), o_ws, grad, u_update, step,
                                F_slot, out3, st) != 0)
             return cuda_fail(cudaGetLastError(), "reduce launch");
-    } else {
-        mark(4);
     }
     mark(5);
     return QOC_OK;

@@ -17,11 +17,15 @@ namespace {
 constexpr int SWEEP_THREADS = 256;
 constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;  // 2 s
 
+// Window sweeps: forward from fwd_init (psi at the window start) through the window's nk slices,
+// storing psi in window slots 0..nk and psi at the window end in fwd_out; backward from bwd_init
+// (lam at the window end) down to the window start, storing lam in slots 0..nk and lam at the window
+// start in bwd_out.  Boundary vectors use the [block][copy][m] layout (DevBlock::v_off).
 template <class T>
 __global__ void __launch_bounds__(SWEEP_THREADS)
-sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__ psi0,
-             const double2* __restrict__ psif, cx<T>* __restrict__ psi_st, cx<T>* __restrict__ lam_st, int dirs,
-             int staged) {
+sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __restrict__ fwd_init, cx<T>* __restrict__ fwd_out,
+             const cx<T>* __restrict__ bwd_init, cx<T>* __restrict__ bwd_out, cx<T>* __restrict__ psi_st,
+             cx<T>* __restrict__ lam_st, int dirs, int staged) {
     extern __shared__ __align__(128) unsigned char dsm[];
     __shared__ __align__(8) uint64_t bar[2];
 
@@ -29,7 +33,7 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
     const bool fwd = (int)blockIdx.x < nfw;
     const int bi = fwd ? (int)blockIdx.x : (int)blockIdx.x - nfw;
     const DevBlock B = P.blocks[bi];
-    const int m = B.m, c = B.c, N = P.N;
+    const int m = B.m, c = B.c, NK = P.nk;
     const long long mmp = B.mmp;
     const uint32_t ubytes = (uint32_t)(mmp * (long long)sizeof(cx<T>));
     cx<T>* ubuf0 = reinterpret_cast<cx<T>*>(dsm);
@@ -38,17 +42,13 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
     cx<T>* y = x + (size_t)m * c;
     const int tid = threadIdx.x;
 
-    const long long cb = P.copy_base[bi];
-    const double2* src = fwd ? psi0 : psif;
-    for (int e = tid; e < m * c; e += blockDim.x) {
-        const int r = e / m, a = e - r * m;
-        x[e] = ccast<T, double>(src[P.copy_src[cb + r] + a]);
-    }
+    const cx<T>* init = (fwd ? fwd_init : bwd_init) + B.v_off;
+    for (int e = tid; e < m * c; e += blockDim.x) x[e] = init[e];
     cx<T>* st = fwd ? psi_st : lam_st;
     const long long s0 = B.s_off;
     __syncthreads();
     {
-        const long long kst = fwd ? 0 : N;
+        const long long kst = fwd ? 0 : NK;
         for (int e = tid; e < m * c; e += blockDim.x) st[s0 + kst * c * m + e] = x[e];
     }
     if (staged) {
@@ -59,9 +59,9 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
         }
         __syncthreads();
         if (tid == 0) {
-            const int k = fwd ? 1 : N;
+            const int i = fwd ? 0 : NK - 1;
             mbar_arrive_expect_tx(&bar[0], ubytes);
-            bulk_copy_g2s(ubuf0, U + B.u_off + (long long)(k - 1) * mmp, ubytes, &bar[0]);
+            bulk_copy_g2s(ubuf0, U + B.u_off + (long long)i * mmp, ubytes, &bar[0]);
         }
     }
     int G = 1;
@@ -69,28 +69,28 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
     const int outs = blockDim.x / G;
     const int part = tid % G;
 
-    for (int t = 0; t < N; ++t) {
-        const int k = fwd ? t + 1 : N - t;
+    for (int t = 0; t < NK; ++t) {
+        const int i = fwd ? t : NK - 1 - t;  // window slot of the propagator applied now
         const cx<T>* Uk;
         if (staged) {
             const int buf = t & 1;
-            if (tid == 0 && t + 1 < N) {
-                const int kn = fwd ? k + 1 : k - 1;
+            if (tid == 0 && t + 1 < NK) {
+                const int in = fwd ? i + 1 : i - 1;
                 fence_proxy_async_smem();
                 mbar_arrive_expect_tx(&bar[buf ^ 1], ubytes);
-                bulk_copy_g2s(buf ? ubuf0 : ubuf1, U + B.u_off + (long long)(kn - 1) * mmp, ubytes, &bar[buf ^ 1]);
+                bulk_copy_g2s(buf ? ubuf0 : ubuf1, U + B.u_off + (long long)in * mmp, ubytes, &bar[buf ^ 1]);
             }
             const bool ok = mbar_wait_bounded(&bar[buf], (uint32_t)((t >> 1) & 1), WAIT_LIMIT_NS);
             if (__syncthreads_or(!ok)) {
                 if (tid == 0) {
                     atomicOr(P.status, ST_TIMEOUT);
-                    if (t + 1 < N) mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)(((t + 1) >> 1) & 1), WAIT_LIMIT_NS);
+                    if (t + 1 < NK) mbar_wait_bounded(&bar[buf ^ 1], (uint32_t)(((t + 1) >> 1) & 1), WAIT_LIMIT_NS);
                 }
                 return;
             }
             Uk = buf ? ubuf1 : ubuf0;
         } else {
-            Uk = U + B.u_off + (long long)(k - 1) * mmp;
+            Uk = U + B.u_off + (long long)i * mmp;
         }
         for (int o0 = 0; o0 < m; o0 += outs) {
             const int o = o0 + tid / G;
@@ -102,7 +102,7 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
                         const cx<T>* row = Uk + (size_t)o * m;
                         for (int j = part; j < m; j += G) cfma<T>(acc, row[j], xr[j]);
                     } else {
-                        for (int i = part; i < m; i += G) cfma_conj<T>(acc, Uk[(size_t)i * m + o], xr[i]);
+                        for (int ii = part; ii < m; ii += G) cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[ii]);
                     }
                 }
                 for (int off = G / 2; off > 0; off >>= 1) {
@@ -113,18 +113,34 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const double2* __restrict__
             }
         }
         __syncthreads();
-        const long long ks = fwd ? k : k - 1;
+        const long long ks = fwd ? i + 1 : i;
         for (int e = tid; e < m * c; e += blockDim.x) {
             x[e] = y[e];
             st[s0 + ks * c * m + e] = y[e];
         }
         __syncthreads();
     }
+    cx<T>* out = (fwd ? fwd_out : bwd_out) + B.v_off;
+    for (int e = tid; e < m * c; e += blockDim.x) out[e] = x[e];
+}
+
+// dst[v_off_b + r*m + a] = (T) src[copy_src(b, r) + a]: the caller's block state -> boundary layout
+template <class T>
+__global__ void gather_kernel(DevPlan P, const double2* __restrict__ src, cx<T>* __restrict__ dst) {
+    for (int bi = blockIdx.y; bi < P.nb; bi += gridDim.y) {
+        const DevBlock& B = P.blocks[bi];
+        const int m = B.m, c = B.c;
+        const long long cb = P.copy_base[bi];
+        for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * c; e += gridDim.x * blockDim.x) {
+            const int r = e / m, a = e - r * m;
+            dst[B.v_off + e] = ccast<T, double>(src[P.copy_src[cb + r] + a]);
+        }
+    }
 }
 
 template <class T>
 __global__ void __launch_bounds__(256)
-overlap_kernel(DevPlan P, const cx<T>* __restrict__ psi_st, const double2* __restrict__ psif, double* out3,
+overlap_kernel(DevPlan P, const cx<T>* __restrict__ fin, const double2* __restrict__ psif, double* out3,
                double2* o_ws) {
     __shared__ double sre[256], sim[256];
     double re = 0.0, im = 0.0;
@@ -132,7 +148,7 @@ overlap_kernel(DevPlan P, const cx<T>* __restrict__ psi_st, const double2* __res
         const DevBlock& B = P.blocks[bi];
         const int m = B.m, c = B.c;
         const long long cb = P.copy_base[bi];
-        const cx<T>* pN = psi_st + B.s_off + (long long)P.N * c * m;
+        const cx<T>* pN = fin + B.v_off;
         for (int e = threadIdx.x; e < m * c; e += blockDim.x) {
             const int r = e / m, a = e - r * m;
             const double2 f = psif[P.copy_src[cb + r] + a];
@@ -162,15 +178,14 @@ overlap_kernel(DevPlan P, const cx<T>* __restrict__ psi_st, const double2* __res
 }
 
 template <class T>
-__global__ void store_final_kernel(DevPlan P, const cx<T>* __restrict__ psi_st, double2* __restrict__ psiN) {
+__global__ void store_final_kernel(DevPlan P, const cx<T>* __restrict__ fin, double2* __restrict__ psiN) {
     for (int bi = 0; bi < P.nb; ++bi) {
         const DevBlock& B = P.blocks[bi];
         const int m = B.m, c = B.c;
         const long long cb = P.copy_base[bi];
-        const cx<T>* pN = psi_st + B.s_off + (long long)P.N * c * m;
         for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * c; e += gridDim.x * blockDim.x) {
             const int r = e / m, a = e - r * m;
-            psiN[P.copy_src[cb + r] + a] = ccast<double, T>(pN[e]);
+            psiN[P.copy_src[cb + r] + a] = ccast<double, T>(fin[B.v_off + e]);
         }
     }
 }
@@ -182,8 +197,8 @@ size_t sweep_smem(int m, int c, int staged, long long mmp) {
 
 }  // namespace
 
-int launch_sweeps(const DevPlan& P, const void* U, const double2* psi0, const double2* psif, void* psi_store,
-                  void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st) {
+int launch_sweeps(const DevPlan& P, const void* U, const void* fwd_init, void* fwd_out, const void* bwd_init,
+                  void* bwd_out, void* psi_store, void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st) {
     const int nblk = ((dirs & 1) ? P.nb : 0) + ((dirs & 2) ? P.nb : 0);
     if (nblk == 0) return 0;
     const long long mmp = ((long long)max_m * max_m + 3) / 4 * 4;
@@ -193,35 +208,45 @@ int launch_sweeps(const DevPlan& P, const void* U, const double2* psi0, const do
         size_t sm = sweep_smem<double>(max_m, max_c, staged, mmp);
         if (sm > limit) return -2;
         cudaFuncSetAttribute(sweep_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        sweep_kernel<double><<<nblk, SWEEP_THREADS, sm, st>>>(P, (const double2*)U, psi0, psif, (double2*)psi_store,
-                                                              (double2*)lam_store, dirs, staged);
+        sweep_kernel<double><<<nblk, SWEEP_THREADS, sm, st>>>(
+            P, (const double2*)U, (const double2*)fwd_init, (double2*)fwd_out, (const double2*)bwd_init,
+            (double2*)bwd_out, (double2*)psi_store, (double2*)lam_store, dirs, staged);
     } else {
         int staged = sweep_smem<float>(max_m, max_c, 1, mmp) <= limit;
         size_t sm = sweep_smem<float>(max_m, max_c, staged, mmp);
         if (sm > limit) return -2;
         cudaFuncSetAttribute(sweep_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        sweep_kernel<float><<<nblk, SWEEP_THREADS, sm, st>>>(P, (const float2*)U, psi0, psif, (float2*)psi_store,
-                                                             (float2*)lam_store, dirs, staged);
+        sweep_kernel<float><<<nblk, SWEEP_THREADS, sm, st>>>(
+            P, (const float2*)U, (const float2*)fwd_init, (float2*)fwd_out, (const float2*)bwd_init,
+            (float2*)bwd_out, (float2*)psi_store, (float2*)lam_store, dirs, staged);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_overlap(const DevPlan& P, const void* psi_store, const double2* psif, double* out3, double2* o_ws,
-                   cudaStream_t st) {
+int launch_gather(const DevPlan& P, const double2* src, void* dst, cudaStream_t st) {
+    dim3 grid(4, P.nb < 1024 ? P.nb : 1024);
     if (P.prec == 0)
-        overlap_kernel<double><<<1, 256, 0, st>>>(P, (const double2*)psi_store, psif, out3, o_ws);
+        gather_kernel<double><<<grid, 256, 0, st>>>(P, src, (double2*)dst);
     else
-        overlap_kernel<float><<<1, 256, 0, st>>>(P, (const float2*)psi_store, psif, out3, o_ws);
+        gather_kernel<float><<<grid, 256, 0, st>>>(P, src, (float2*)dst);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
-int launch_store_final(const DevPlan& P, const void* psi_store, double2* psiN, long long state_len,
-                       cudaStream_t st) {
+int launch_overlap(const DevPlan& P, const void* fin, const double2* psif, double* out3, double2* o_ws,
+                   cudaStream_t st) {
+    if (P.prec == 0)
+        overlap_kernel<double><<<1, 256, 0, st>>>(P, (const double2*)fin, psif, out3, o_ws);
+    else
+        overlap_kernel<float><<<1, 256, 0, st>>>(P, (const float2*)fin, psif, out3, o_ws);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_store_final(const DevPlan& P, const void* fin, double2* psiN, long long state_len, cudaStream_t st) {
     if (cudaMemsetAsync(psiN, 0, (size_t)state_len * sizeof(double2), st) != cudaSuccess) return -1;
     if (P.prec == 0)
-        store_final_kernel<double><<<8, 256, 0, st>>>(P, (const double2*)psi_store, psiN);
+        store_final_kernel<double><<<8, 256, 0, st>>>(P, (const double2*)fin, psiN);
     else
-        store_final_kernel<float><<<8, 256, 0, st>>>(P, (const float2*)psi_store, psiN);
+        store_final_kernel<float><<<8, 256, 0, st>>>(P, (const float2*)fin, psiN);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
