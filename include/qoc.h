@@ -128,9 +128,11 @@ int qoc_dicke_state(const qoc_basis* basis, int k, double* blk);
 typedef struct qoc_plan qoc_plan;
 
 enum {
-    QOC_PREC_F64 = 0,  /* all steps in FP64 */
-    QOC_PREC_F32 = 1   /* complex FP32 Taylor polynomial and sweeps; FP64 squaring chain,
-                          overlap, fidelity and gradient accumulation */
+    QOC_PREC_F64 = 0,     /* all steps in FP64 */
+    QOC_PREC_F32 = 1,     /* complex FP32 Taylor polynomial and sweeps; FP64 squaring chain,
+                             overlap, fidelity and gradient accumulation */
+    QOC_PREC_F32_ALL = 2  /* as QOC_PREC_F32 but the squaring chain in FP32 too (small blocks with
+                             few squarings; FP64 overlap and accumulation) */
 };
 
 /* Options of a plan; zero-initialise and set what you need (qoc_plan_opts_default fills it). */
@@ -156,6 +158,18 @@ void qoc_plan_opts_default(qoc_plan_opts* opts);
  * Errors: QOC_EINVAL, QOC_EUNSUPPORTED (a block larger than the kernels support), QOC_ECUDA. */
 int qoc_plan_create(const qoc_basis* basis, int N, double dt, const qoc_plan_opts* opts,
                     const uint8_t* active, qoc_plan** out);
+
+/* A plan over many independent problems that run together in every launch (batched GRAPE):
+ * problem i has basis bases[i], Ns[i] slices of length dts[i] and active copies actives[i] (host,
+ * may be NULL, as may the array itself).  Every basis must have the same number of controls.
+ * Device buffers of a batch plan concatenate the problems in order: pulses and gradients
+ * [sum_i Ns[i]][n_ctrl], block states [sum_i state_len_i], out3 [n_problems][3].  Checkpointing
+ * (ckpt_segment != 0) needs a single problem. */
+int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const int* Ns, const double* dts,
+                          const qoc_plan_opts* opts, const uint8_t* const* actives, qoc_plan** out);
+
+/* Problems, total pulse rows (sum of N) and concatenated block-state length of a plan. */
+int qoc_plan_info(const qoc_plan* plan, int* n_problems, int64_t* pulse_rows, int64_t* state_len);
 void qoc_plan_free(qoc_plan* plan);
 
 /* Bytes of device workspace the plan's calls need (propagators, states and costates, partial
@@ -183,21 +197,41 @@ int qoc_propagate(const qoc_plan* plan, const double* u, const double* psi0, dou
                   void* workspace, size_t workspace_bytes, void* stream);
 
 /* Fidelity and gradient (Eq. probability; Appendix B):
- *   out3 (dev, 3 doubles) = { F, Re o, Im o },  o = sum over active copies <psif|psi_N>,  F = |o|^2
+ *   out3 (dev, 3 doubles per problem) = { F, Re o, Im o },  o = sum over the problem's active copies
+ *   <psif|psi_N>,  F = |o|^2
  *   grad (dev [N][n_ctrl], may be NULL) = dF/du_kj = 2 Re(conj(o) sum lam_k^dagger dU_k/du_kj psi_{k-1})
  * psi0, psif: dev block states (state_len complex128). */
 int qoc_fidelity_and_grad(const qoc_plan* plan, const double* u, const double* psi0,
                           const double* psif, double* out3, double* grad, void* workspace,
                           size_t workspace_bytes, void* stream);
 
-/* Gradient ascent (GRAPE, Sec. II.A): for it = 0..iters-1: compute F and dF/du, record F in
- * F_hist[it] (dev, iters doubles), then u <- u + step * dF/du.  u (dev [N][n_ctrl]) is updated
- * in place.  With f_target <= 1 the loop checks F every check_every iterations on the host and
- * stops once F >= f_target; *iters_done receives the number of updates made (host, may be NULL).
- * Returns QOC_ENOTCONVERGED if f_target <= 1 and was not reached. */
-int qoc_optimize_pulses(const qoc_plan* plan, double* u, const double* psi0, const double* psif,
-                        int iters, double step, double f_target, int check_every, double* F_hist,
-                        int* iters_done, void* workspace, size_t workspace_bytes, void* stream);
+/* Gradient ascent (GRAPE, Sec. II.A) on every problem of the plan. */
+enum { QOC_RULE_FIXED = 0,   /* u <- u + step * dF/du */
+       QOC_RULE_ADAM = 1 };  /* Adam ascent: moments of dF/du with beta1, beta2, eps; u <- u + step * m^/(sqrt(v^)+eps) */
+
+typedef struct qoc_opt_opts {
+    int iters;             /* iterations at most */
+    int rule;              /* QOC_RULE_FIXED or QOC_RULE_ADAM */
+    double step, beta1, beta2, eps;
+    double f_target;       /* <= 1: stop once every problem reached F >= f_target (checked on the host
+                              every check_every iterations); > 1: run all iterations */
+    int check_every;
+    int use_graph;         /* 1: capture one iteration into a CUDA graph once and replay it (needs a
+                              non-default stream; the graph is kept while the arguments stay the same) */
+    int freeze_converged;  /* 1 (default): a problem that reached f_target keeps its pulses */
+    int reserved[3];
+} qoc_opt_opts;
+
+void qoc_opt_opts_default(qoc_opt_opts* opts);
+
+/* For it = 0..iters-1: F and dF/du of every problem, F_hist[it][p] = F_p (dev, iters*n_problems
+ * doubles), then the update of u (dev [rows][n_ctrl], in place) unless problem p is frozen.
+ * reached (dev, n_problems ints, may be NULL): first iteration whose F_p >= f_target, -1 if none.
+ * *iters_done (host, may be NULL) receives the iterations run.  Returns QOC_ENOTCONVERGED if
+ * f_target <= 1 and some problem did not reach it. */
+int qoc_optimize_pulses(qoc_plan* plan, double* u, const double* psi0, const double* psif, const qoc_opt_opts* opts,
+                        double* F_hist, int* reached, int* iters_done, void* workspace, size_t workspace_bytes,
+                        void* stream);
 
 /* ---------------------------------------------------------------- measurement */
 /* Phase timing: when enabled, every later call records CUDA events on its stream between its

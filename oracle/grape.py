@@ -159,6 +159,36 @@ def gradient_fd(problem, u: np.ndarray, tau: float, entries, h: float = 1e-6) ->
     return np.array(out)
 
 
+def adam_update(u, g, m, v, t, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam ascent step (Kingma & Ba, 2015) on u with gradient g; t counts from 1.  The paper
+    leaves the optimiser to its supplement; this is the library's documented choice besides the
+    fixed step.  Returns (u, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    mh = m / (1.0 - beta1 ** t)
+    vh = v / (1.0 - beta2 ** t)
+    return u + step * mh / (np.sqrt(vh) + eps), m, v
+
+
+def grape_adam(problem, u0: np.ndarray, tau: float, iters: int, step: float, f_target: float = 2.0,
+               beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+    """Adam ascent on F; stops updating once F >= f_target.  Returns (u, [F per iteration], first
+    iteration with F >= f_target or -1)."""
+    u = np.array(u0, dtype=np.float64, copy=True)
+    m = np.zeros_like(u)
+    v = np.zeros_like(u)
+    hist = []
+    reached = -1
+    for it in range(iters):
+        F, _, g = fidelity_and_grad(problem, u, tau)
+        hist.append(F)
+        if F >= f_target:
+            reached = it
+            break
+        u, m, v = adam_update(u, g, m, v, it + 1, step, beta1, beta2, eps)
+    return u, hist, reached
+
+
 def grape(problem, u0: np.ndarray, tau: float, iters: int, step: float, f_target: float = 2.0):
     """Fixed-step gradient ascent u <- u + step * dF/du; stops early once F >= f_target.
     Returns (u, [F before each update], iterations run)."""

@@ -21,6 +21,9 @@ QOC_ENOTCONVERGED = -6
 
 QOC_PREC_F64 = 0
 QOC_PREC_F32 = 1
+QOC_PREC_F32_ALL = 2
+QOC_RULE_FIXED = 0
+QOC_RULE_ADAM = 1
 QOC_BASIS_FIRST_BLOCK_ONLY = 1
 QOC_BASIS_NO_VECTORS = 2
 
@@ -40,6 +43,12 @@ class qoc_plan_opts(C.Structure):
                 ("ckpt_segment", C.c_int), ("reserved", C.c_int * 4)]
 
 
+class qoc_opt_opts(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rule", C.c_int), ("step", C.c_double), ("beta1", C.c_double),
+                ("beta2", C.c_double), ("eps", C.c_double), ("f_target", C.c_double), ("check_every", C.c_int),
+                ("use_graph", C.c_int), ("freeze_converged", C.c_int), ("reserved", C.c_int * 3)]
+
+
 # name -> (restype, argtypes); every symbol include/qoc.h declares
 P = C.c_void_p
 D = C.POINTER(C.c_double)
@@ -56,6 +65,9 @@ SIGNATURES = {
     "qoc_dicke_state": (C.c_int, [P, C.c_int, P]),
     "qoc_plan_opts_default": (None, [C.POINTER(qoc_plan_opts)]),
     "qoc_plan_create": (C.c_int, [P, C.c_int, C.c_double, C.POINTER(qoc_plan_opts), P, C.POINTER(P)]),
+    "qoc_plan_create_batch": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_double),
+                                         C.POINTER(qoc_plan_opts), C.POINTER(P), C.POINTER(P)]),
+    "qoc_plan_info": (C.c_int, [P, C.POINTER(C.c_int), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "qoc_plan_free": (None, [P]),
     "qoc_plan_workspace_bytes": (C.c_int, [P, C.POINTER(C.c_size_t)]),
     "qoc_plan_sync_status": (C.c_int, [P, P]),
@@ -63,8 +75,9 @@ SIGNATURES = {
     "qoc_expm_blocks": (C.c_int, [P, P, P, P, C.c_size_t, P]),
     "qoc_propagate": (C.c_int, [P, P, P, P, P, C.c_size_t, P]),
     "qoc_fidelity_and_grad": (C.c_int, [P, P, P, P, P, P, P, C.c_size_t, P]),
-    "qoc_optimize_pulses": (C.c_int, [P, P, P, P, C.c_int, C.c_double, C.c_double, C.c_int, P,
-                                      C.POINTER(C.c_int), P, C.c_size_t, P]),
+    "qoc_opt_opts_default": (None, [C.POINTER(qoc_opt_opts)]),
+    "qoc_optimize_pulses": (C.c_int, [P, P, P, P, C.POINTER(qoc_opt_opts), P, P, C.POINTER(C.c_int), P,
+                                      C.c_size_t, P]),
     "qoc_plan_set_profiling": (C.c_int, [P, C.c_int]),
     "qoc_plan_phase_times": (C.c_int, [P, C.POINTER(C.c_float), C.c_int]),
     "qoc_plan_work_counts": (C.c_int, [P, C.POINTER(C.c_longlong), C.c_int]),

@@ -105,35 +105,53 @@ class Basis:
 
 
 class Plan:
-    """A GPU plan: basis, N slices of length dt, precision, and the active block copies."""
+    """A GPU plan: one problem (basis, N slices of length dt, active copies) or a batch of them that
+    run together in every launch.  Batched device buffers concatenate the problems in order."""
 
-    def __init__(self, basis: Basis, N: int, dt: float, prec: str = "f64", grad_mode: int = 0,
-                 active: Optional[np.ndarray] = None, max_squarings: int = 16, ckpt_segment: int = 0,
-                 device=None):
+    PRECS = {"f64": L.QOC_PREC_F64, "f32": L.QOC_PREC_F32, "f32_all": L.QOC_PREC_F32_ALL}
+
+    def __init__(self, basis, N, dt, prec: str = "f64", grad_mode: int = 0, active=None,
+                 max_squarings: int = 16, ckpt_segment: int = 0, device=None):
         self.lib = L.load()
-        self.basis = basis
-        self.N, self.dt = N, dt
+        batch = not isinstance(basis, Basis)
+        self.bases = list(basis) if batch else [basis]
+        self.basis = self.bases[0]
+        n = len(self.bases)
+        Ns = list(N) if batch else [N]
+        dts = list(dt) if batch else [dt]
+        acts = (list(active) if active is not None else [None] * n) if batch else [active]
+        self.N, self.dt = (Ns[0], dts[0]) if not batch else (Ns, dts)
+        self.Ns, self.dts = Ns, dts
         self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
         opts = L.qoc_plan_opts()
         self.lib.qoc_plan_opts_default(C.byref(opts))
-        opts.prec = L.QOC_PREC_F64 if prec == "f64" else L.QOC_PREC_F32
+        opts.prec = self.PRECS[prec]
         opts.grad_mode = grad_mode
         opts.max_squarings = max_squarings
         opts.ckpt_segment = ckpt_segment
         self.prec = prec
-        act = None
-        if active is not None:
-            self._active = np.ascontiguousarray(active, dtype=np.uint8)
-            assert self._active.shape == (basis.n_copies,)
-            act = self._active.ctypes.data_as(C.c_void_p)
+        self._acts = [None if a_ is None else np.ascontiguousarray(a_, dtype=np.uint8) for a_ in acts]
+        for a_, b_ in zip(self._acts, self.bases):
+            assert a_ is None or a_.shape == (b_.n_copies,)
+        self._active = self._acts[0]
+        act_ptrs = (C.c_void_p * n)(*[None if a_ is None else a_.ctypes.data_as(C.c_void_p).value for a_ in self._acts])
+        base_ptrs = (C.c_void_p * n)(*[b_.handle.value for b_ in self.bases])
+        Ns_c = (C.c_int * n)(*Ns)
+        dts_c = (C.c_double * n)(*dts)
         h = C.c_void_p()
         with torch.cuda.device(self.device):
-            L.check(self.lib.qoc_plan_create(basis.handle, N, dt, C.byref(opts), act, C.byref(h)), "qoc_plan_create")
+            L.check(self.lib.qoc_plan_create_batch(base_ptrs, n, Ns_c, dts_c, C.byref(opts), act_ptrs, C.byref(h)),
+                    "qoc_plan_create_batch")
         self.handle = h
+        npb, rows, sl = C.c_int(), C.c_int64(), C.c_int64()
+        L.check(self.lib.qoc_plan_info(h, C.byref(npb), C.byref(rows), C.byref(sl)), "qoc_plan_info")
+        self.n_prob, self.rows, self.state_len = npb.value, rows.value, sl.value
         nbytes = C.c_size_t()
         L.check(self.lib.qoc_plan_workspace_bytes(h, C.byref(nbytes)), "qoc_plan_workspace_bytes")
         self.workspace_bytes = nbytes.value
         self._ws = None
+        self._graph_stream = None
+        self.last_reached = None
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -151,20 +169,20 @@ class Plan:
 
     def _check_u(self, u: torch.Tensor):
         assert u.dtype == torch.float64 and u.is_cuda and u.is_contiguous()
-        assert tuple(u.shape) == (self.N, self.basis.n_ctrl), (tuple(u.shape), (self.N, self.basis.n_ctrl))
+        assert tuple(u.shape) == (self.rows, self.basis.n_ctrl), (tuple(u.shape), (self.rows, self.basis.n_ctrl))
 
     def _check_state(self, s: torch.Tensor):
         assert s.dtype == torch.complex128 and s.is_cuda and s.is_contiguous()
-        assert s.numel() == self.basis.state_len
+        assert s.numel() == self.state_len
 
     def fidelity_and_grad(self, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, want_grad: bool = True,
                           out3: Optional[torch.Tensor] = None, grad: Optional[torch.Tensor] = None, stream=None):
-        """(out3 = [F, Re o, Im o], grad [N, nc]) on the device, asynchronously on the stream."""
+        """(out3 = [F, Re o, Im o] per problem, grad [rows, nc]) on the device, asynchronously."""
         self._check_u(u)
         self._check_state(psi0)
         self._check_state(psif)
         if out3 is None:
-            out3 = torch.empty(3, dtype=torch.float64, device=u.device)
+            out3 = torch.empty(3 * self.n_prob, dtype=torch.float64, device=u.device)
         if want_grad and grad is None:
             grad = torch.empty_like(u)
         ws = self.workspace
@@ -214,19 +232,41 @@ class Plan:
         return sum(self.N * self.basis.blocks[b][1] ** 2 for b in self.active_blocks())
 
     def optimize(self, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, iters: int, step: float,
-                 f_target: float = 2.0, check_every: int = 10, stream=None):
-        """GRAPE ascent in place on u; returns (F history tensor [iters_done], iterations done, converged)."""
+                 f_target: float = 2.0, check_every: int = 10, rule: str = "fixed", beta1: float = 0.9,
+                 beta2: float = 0.999, eps: float = 1e-8, use_graph: bool = False, freeze: bool = True,
+                 stream=None):
+        """GRAPE ascent in place on u.  Returns (F history [iters_done] for one problem, else
+        [iters_done, n_prob], iterations done, converged); self.last_reached holds, per problem, the
+        first iteration whose F reached f_target (-1 if none)."""
         self._check_u(u)
-        F_hist = torch.zeros(max(iters, 1), dtype=torch.float64, device=u.device)
+        self._check_state(psi0)
+        self._check_state(psif)
+        F_hist = torch.zeros(max(iters, 1) * self.n_prob, dtype=torch.float64, device=u.device)
+        reached = torch.empty(self.n_prob, dtype=torch.int32, device=u.device)
+        o = L.qoc_opt_opts()
+        self.lib.qoc_opt_opts_default(C.byref(o))
+        o.iters, o.rule, o.step = iters, (L.QOC_RULE_ADAM if rule == "adam" else L.QOC_RULE_FIXED), step
+        o.beta1, o.beta2, o.eps, o.f_target = beta1, beta2, eps, f_target
+        o.check_every, o.use_graph, o.freeze_converged = check_every, int(use_graph), int(freeze)
         done = C.c_int(0)
         ws = self.workspace
-        rc = self.lib.qoc_optimize_pulses(self.handle, _ptr(u), _ptr(psi0), _ptr(psif), iters, step, f_target,
-                                          check_every, _ptr(F_hist), C.byref(done), _ptr(ws), ws.numel(),
-                                          _stream(stream))
+        cur = torch.cuda.current_stream() if stream is None else stream
+        run_stream = cur
+        if use_graph:
+            if self._graph_stream is None:
+                self._graph_stream = torch.cuda.Stream(device=self.device)
+            run_stream = self._graph_stream
+            run_stream.wait_stream(cur)
+        rc = self.lib.qoc_optimize_pulses(self.handle, _ptr(u), _ptr(psi0), _ptr(psif), C.byref(o), _ptr(F_hist),
+                                          _ptr(reached), C.byref(done), _ptr(ws), ws.numel(), _stream(run_stream))
+        if use_graph:
+            cur.wait_stream(run_stream)
         converged = rc == L.QOC_OK
         if rc not in (L.QOC_OK, L.QOC_ENOTCONVERGED):
             L.check(rc, "qoc_optimize_pulses")
-        return F_hist[:done.value], done.value, converged
+        self.last_reached = reached
+        Fh = F_hist[: done.value * self.n_prob].view(done.value, self.n_prob)
+        return (Fh[:, 0] if self.n_prob == 1 else Fh), done.value, converged
 
     def set_profiling(self, on: bool = True) -> None:
         L.check(self.lib.qoc_plan_set_profiling(self.handle, int(on)), "qoc_plan_set_profiling")

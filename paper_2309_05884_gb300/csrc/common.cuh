@@ -45,39 +45,61 @@ enum : int {
     ST_TIMEOUT = 8,         // a bounded wait on an asynchronous copy gave up
 };
 
-// Per-active-block table, in device memory (one entry per active block).
+// Per-active-block table, in device memory (one entry per active block of every problem).
 struct DevBlock {
     int m;            // size
     int c;            // active copies
-    int b;            // index in the basis
+    int b;            // index in its problem's basis
+    int prob;         // problem index
+    int N;            // slices of the problem
     int pad;
+    double dt;        // slice length tau of the problem
+    int64_t u_row;    // first row of the problem in the concatenated pulse array [sum_p N_p][nc]
+    int64_t part_off; // first row of this block in the slice-derivative array [sum_b N_b][nc]
     int64_t mmp;      // padded stride (elements) between consecutive U_b[k]: m*m rounded up to 4
     int64_t h_off;    // complex offset of H0_b in the packed Hamiltonian array; Hc_jb at h_off + (1+j)*m*m
-    int64_t u_off;    // complex offset of U_b[k=0] in the propagator area (U_b[k] at u_off + k*mmp)
+    int64_t u_off;    // complex offset of U_b[slot 0] in the propagator area (slot i at u_off + i*mmp)
     int64_t s_off;    // complex offset of psi_b[slot 0] in the window state areas (slot i at s_off + i*c*m)
     int64_t v_off;    // complex offset of block b in a boundary-vector array [b][copy][m]
     double h0_norm1;  // max column 1-norm of H0_b
     double hc_norm1[8];
 };
 
+// GRAPE update rule applied by the reduction kernel (after F and dF/du of an iteration).
+struct UpdateRule {
+    int kind;         // 0: u += step * g;  1: Adam ascent with (beta1, beta2, eps)
+    int freeze;       // 1: problems whose F reached f_target keep their pulses
+    double step, beta1, beta2, eps, f_target;
+    int* iter;        // device iteration counter (Adam bias correction, F history slot)
+    int* reached;     // [n_prob] first iteration with F >= f_target (-1 = not yet), or null
+    double* adam_m;   // [rows][nc] first moments
+    double* adam_v;   // [rows][nc] second moments
+    double* F_hist;   // [iters][n_prob] or null
+};
+
 // Everything a kernel needs about the plan, passed by value.
 struct DevPlan {
-    int N;            // slices
+    int N;            // slices (single-problem plans; batches use DevBlock::N)
     int k0;           // first slice (0-based) of the current window
-    int nk;           // slices in the current window
+    int nk;           // slices in the current window; < 0: every block's whole problem
     int nc;           // controls
     int nb;           // active blocks
+    int n_prob;       // problems
     int prec;         // QOC_PREC_*
-    double dt;        // tau
     int max_sq;       // squaring cap
     int grad_mode;
+    double dt;        // tau (single-problem plans)
     const DevBlock* blocks;
     const int64_t* copy_src;   // [sum_b c_b] source offsets of active copies (complex elements), block-major
     const int64_t* copy_base;  // [nb] start of block b's entries in copy_src
+    const int2* items;         // (block, slice) list over all blocks (whole-problem launches)
+    long long n_items;
+    const int* prob_blocks;    // active blocks of problem p at prob_blocks[prob_block_off[p] .. [p+1])
+    const int* prob_block_off;
     const void* H;             // packed block Hamiltonians in the working precision
     const double2* H64;        // the same in FP64
     int* status;
-    unsigned long long* stats;  // work counters or null
+    unsigned long long* stats; // work counters or null
 };
 
 }  // namespace qoc

@@ -21,7 +21,8 @@ __constant__ int c_deg_q[9] = {1, 2, 2, 3, 3, 4, 4, 5, 6};
 template <class T, int R>
 __global__ void __launch_bounds__(GEMM_THREADS)
 expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int* __restrict__ cls_blocks,
-            int n_cls, void* __restrict__ Uout, char* __restrict__ scratch, size_t slot_bytes, int m_max) {
+            int n_cls, const int2* __restrict__ cls_items, long long n_cls_items, void* __restrict__ Uout,
+            char* __restrict__ scratch, size_t slot_bytes, int m_max) {
     constexpr int RD = R > 4 ? 4 : R;  // FP64 squaring tile
     constexpr size_t SMB = sizeof(GemmSmem<T, R>) > sizeof(GemmSmem<double, RD>) ? sizeof(GemmSmem<T, R>)
                                                                                    : sizeof(GemmSmem<double, RD>);
@@ -35,8 +36,11 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     __shared__ double s_scale;
     __shared__ int s_sq, s_p, s_q;
 
+    // whole-problem launches walk the class's (block, slice) list; windowed launches (one problem,
+    // checkpoint segments) index the window directly
+    const bool whole = P.nk < 0;
     const int NK = P.nk;
-    const long long total = (long long)n_cls * NK;
+    const long long total = whole ? n_cls_items : (long long)n_cls * NK;
     char* slot = scratch + (size_t)blockIdx.x * slot_bytes;
     const size_t mm_max = (size_t)m_max * m_max;
     cx<T>* base = reinterpret_cast<cx<T>*>(slot);
@@ -53,9 +57,17 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     if (threadIdx.x < 8) pw[threadIdx.x] = base + (size_t)(threadIdx.x < 6 ? threadIdx.x : 0) * mm_max;
 
     for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        const int bi = cls_blocks[item / NK];
-        const int kw = (int)(item % NK);  // slot in the window
-        const int k = P.k0 + kw;          // slice (0-based)
+        int bi, kw, k;  // block, slot in the window, slice (0-based)
+        if (whole) {
+            const int2 it = cls_items[item];
+            bi = it.x;
+            kw = it.y;
+            k = it.y;
+        } else {
+            bi = cls_blocks[item / NK];
+            kw = (int)(item % NK);
+            k = P.k0 + kw;
+        }
         const DevBlock& B = P.blocks[bi];
         const int m = B.m;
         const size_t mm = (size_t)m * m;
@@ -64,14 +76,14 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
             double beta = B.h0_norm1;
             int bad = 0;
             for (int j = 0; j < P.nc; ++j) {
-                const double uk = u[(size_t)k * P.nc + j];
+                const double uk = u[(size_t)(B.u_row + k) * P.nc + j];
                 const int fin = isfinite(uk);
                 bad |= !fin;
                 s_uk[j] = fin ? uk : 0.0;
                 beta += fabs(s_uk[j]) * B.hc_norm1[j];
             }
             if (bad) atomicOr(P.status, ST_NAN_PULSE);
-            beta *= P.dt;
+            beta *= B.dt;
             int s = 0;
             while (beta > tabs.theta_cap && s < P.max_sq) { beta *= 0.5; ++s; }
             if (beta > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
@@ -80,7 +92,7 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
             s_sq = s;
             s_p = c_deg_p[di];
             s_q = c_deg_q[di];
-            s_scale = P.dt / (double)(1LL << s);
+            s_scale = B.dt / (double)(1LL << s);
             if (P.stats) {
                 const unsigned long long m3 = (unsigned long long)m * m * m;
                 atomicAdd(P.stats + 0, m3 * (unsigned long long)(c_deg_p[di] + c_deg_q[di] - 2));
@@ -146,6 +158,13 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
         cx<T>* Uo = reinterpret_cast<cx<T>*>(Uout) + B.u_off + (size_t)kw * B.mmp;
         if (s == 0) {
             for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
+        } else if (!tabs.sq_f64 && sizeof(T) == sizeof(float)) {
+            // squaring chain in the working precision
+            for (int i = 0; i < s; ++i) {
+                cta_gemm<T, R>(Sn, S, S, m, 0, nullptr, nullptr, sm);
+                cx<T>* t = S; S = Sn; Sn = t;
+            }
+            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
         } else {
             for (size_t e = threadIdx.x; e < mm; e += blockDim.x) D0[e] = ccast<double, T>(S[e]);
             __syncthreads();
@@ -163,8 +182,10 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
 
 template <class T, int R>
 int launch_one(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
-               void* Uout, char* scratch, size_t slot_bytes, int m_max, int grid, cudaStream_t st) {
-    expm_kernel<T, R><<<grid, GEMM_THREADS, 0, st>>>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max);
+               const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
+               int grid, cudaStream_t st) {
+    expm_kernel<T, R><<<grid, GEMM_THREADS, 0, st>>>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch,
+                                                     slot_bytes, m_max);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -174,15 +195,17 @@ __global__ void export_u_kernel(DevPlan P, const cx<T>* __restrict__ U, double2*
     const int bi = blockIdx.y;
     const DevBlock& B = P.blocks[bi];
     const size_t mm = (size_t)B.m * B.m;
-    for (int k = blockIdx.x; k < P.nk; k += gridDim.x)
+    const int nk = P.nk < 0 ? B.N : P.nk;
+    const int k0 = P.nk < 0 ? 0 : P.k0;
+    for (int k = blockIdx.x; k < nk; k += gridDim.x)
         for (size_t e = threadIdx.x; e < mm; e += blockDim.x)
-            out[a_off[bi] + (size_t)(P.k0 + k) * mm + e] = ccast<double, T>(U[B.u_off + (size_t)k * B.mmp + e]);
+            out[a_off[bi] + (size_t)(k0 + k) * mm + e] = ccast<double, T>(U[B.u_off + (size_t)k * B.mmp + e]);
 }
 
 }  // namespace
 
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st) {
-    dim3 grid(P.nk < 1024 ? P.nk : 1024, P.nb);
+    dim3 grid(256, P.nb);
     if (P.prec == 0)
         export_u_kernel<double><<<grid, 256, 0, st>>>(P, (const double2*)U, U_out, a_off);
     else
@@ -221,25 +244,28 @@ int expm_grid_limit(int prec, int R) {
     return sms * occ;
 }
 
-int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls, int R,
-                void* Uout, char* scratch, size_t slot_bytes, int m_max, int grid, cudaStream_t st) {
+int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
+                const int2* items, long long n_items, int R, void* Uout, char* scratch, size_t slot_bytes, int m_max,
+                int grid, cudaStream_t st) {
+#define QOC_L(TT, RR) launch_one<TT, RR>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes, m_max, grid, st)
     if (P.prec == 0) {
         switch (R) {
-            case 1: return launch_one<double, 1>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-            case 2: return launch_one<double, 2>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-            case 3: return launch_one<double, 3>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-            default: return launch_one<double, 4>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
+            case 1: return QOC_L(double, 1);
+            case 2: return QOC_L(double, 2);
+            case 3: return QOC_L(double, 3);
+            default: return QOC_L(double, 4);
         }
     }
     switch (R) {
-        case 1: return launch_one<float, 1>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        case 2: return launch_one<float, 2>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        case 3: return launch_one<float, 3>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        case 4: return launch_one<float, 4>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        case 5: return launch_one<float, 5>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        case 6: return launch_one<float, 6>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
-        default: return launch_one<float, 7>(P, tabs, u, cls, n_cls, Uout, scratch, slot_bytes, m_max, grid, st);
+        case 1: return QOC_L(float, 1);
+        case 2: return QOC_L(float, 2);
+        case 3: return QOC_L(float, 3);
+        case 4: return QOC_L(float, 4);
+        case 5: return QOC_L(float, 5);
+        case 6: return QOC_L(float, 6);
+        default: return QOC_L(float, 7);
     }
+#undef QOC_L
 }
 
 }  // namespace qoc

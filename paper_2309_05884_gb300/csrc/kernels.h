@@ -14,14 +14,18 @@ struct ExpmTables {
     double theta[9];
     int n_deg;          // degrees allowed (prefix of the table)
     double theta_cap;   // largest norm the polynomial is evaluated at; larger norms are scaled
+    int sq_f64;         // 1: squaring chain in FP64; 0: in the working precision
 };
 
 // ---- expm.cu
 size_t expm_slot_bytes(int prec, int m_max);
 int expm_r_for(int prec, int m);
 int expm_grid_limit(int prec, int R);
-int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls, int R,
-                void* Uout, char* scratch, size_t slot_bytes, int m_max, int grid, cudaStream_t st);
+// One launch per size class R: cls lists the class's blocks (windowed launches), items its
+// (block, slice) pairs (whole-problem launches, P.nk < 0).
+int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
+                const int2* items, long long n_items, int R, void* Uout, char* scratch, size_t slot_bytes, int m_max,
+                int grid, cudaStream_t st);
 // U_out[a_off[b] + k*m*m + e] (complex128, unpadded) <- the working-precision propagators.
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st);
 
@@ -48,9 +52,10 @@ size_t grad_slot_bytes(int prec, int max_m);
 // Shared memory the slice-derivative kernel needs for its vector families (without A).
 size_t grad_vector_smem(int prec, int max_m);
 int grad_grid_limit(int prec, int max_m);
-// grad[k][j] = 2 Re(conj(o) sum_b do[k][b][j]); if step != 0 also u[k][j] += step * grad[k][j].
+// Per problem p: grad[k][j] = 2 Re(conj(o_p) sum over p's blocks of the slice derivatives); then
+// the update rule on u (rule.kind < 0: none); advances rule.iter when it is set.
 int launch_grad_reduce(const DevPlan& P, const double2* partial, const double2* o_ws, double* grad, double* u,
-                       double step, double* F_hist_slot, const double* out3, cudaStream_t st);
+                       const UpdateRule& rule, const double* out3, cudaStream_t st);
 // A_out[b][k] = -i dt (H0_b + sum_j u_kj Hc_jb) in complex128.
 int launch_assemble(const DevPlan& P, const double* u, double2* A_out, const long long* a_off, cudaStream_t st);
 

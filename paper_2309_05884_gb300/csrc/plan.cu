@@ -1,6 +1,9 @@
-// GPU plan: the active blocks of a basis for a fixed slice count and slice length, their
-// Hamiltonians resident in device memory, the workspace layout, and the C ABI entry points that
-// chain the kernels (assembly + expm -> sweeps -> overlap -> slice derivatives -> reduction).
+// GPU plan: the active blocks of one or many problems (each a basis with its own slice count N and
+// slice length tau), their Hamiltonians resident in device memory, the workspace layout, and the C
+// ABI entry points that chain the kernels:
+//   gather states -> assembly + expm (one launch per size class) -> forward/backward sweeps ->
+//   FP64 overlap per problem -> exact slice derivatives -> reduction (+ GRAPE update).
+// With one problem and a checkpoint segment S < N the same kernels run on slice windows.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -15,17 +18,42 @@ using namespace qoc;
 
 struct ExpmClass {
     int R;
-    int offset;   // into the class-list array
-    int count;    // active blocks in the class
+    int offset;          // into the class block list (windowed launches)
+    int count;           // active blocks in the class
+    long long item_off;  // into the class item list (whole-problem launches)
+    long long n_items;
     int m_max;
     int grid;
     size_t slot_bytes;
 };
 
+struct Problem {
+    const qoc_basis* basis;
+    int N;
+    double dt;
+    int64_t state_off;  // complex offset of this problem's block state in the concatenated states
+    int64_t u_row;      // first pulse row
+};
+
+struct GraphKey {
+    const void* u;
+    const void* psi0;
+    const void* psif;
+    const void* F_hist;
+    const void* reached;
+    const void* ws;
+    double step, beta1, beta2, eps, f_target;
+    int kind, freeze;
+    cudaStream_t stream;
+};
+
 struct qoc_plan {
-    const qoc_basis* basis = nullptr;
+    std::vector<Problem> probs;
+    int n_prob = 0;
+    int64_t rows = 0;       // sum_p N_p (pulse rows)
+    int64_t state_len = 0;  // concatenated block-state length
     int device = 0;
-    int N = 0;
+    int N = 0;              // slices of a single-problem plan (max over problems otherwise)
     double dt = 0.0;
     qoc_plan_opts opts{};
     int nc = 0;
@@ -35,12 +63,13 @@ struct qoc_plan {
     std::vector<DevBlock> hblocks;
     std::vector<int64_t> copy_src, copy_base;
     std::vector<long long> a_off;  // export layout offsets (complex), per active block
-    int64_t export_elems = 0;      // N * sum m^2 over active blocks
+    std::vector<int2> items;       // (block, slice) over all blocks
+    std::vector<int> prob_blocks, prob_block_off;
     ExpmTables tabs{};
     std::vector<ExpmClass> classes;
     int grad_grid = 0;
     size_t grad_slot = 0;
-    int seg = 0;                    // slices per checkpoint segment (== N without checkpointing)
+    int seg = 0;                    // slices per checkpoint segment (single problem)
     int nseg = 1;                   // segments
     int64_t vlen = 0;               // complex elements of one boundary vector set (sum c*m)
     // device
@@ -51,23 +80,31 @@ struct qoc_plan {
     void* d_H = nullptr;
     double2* d_H64 = nullptr;
     int* d_cls = nullptr;
+    int2* d_cls_items = nullptr;
+    int2* d_items = nullptr;
+    int* d_prob_blocks = nullptr;
+    int* d_prob_block_off = nullptr;
     int* d_status = nullptr;
     unsigned long long* d_stats = nullptr;
     bool profiling = false;
+    bool capturing = false;
     cudaEvent_t ev[6] = {};
+    cudaGraphExec_t graph = nullptr;
+    GraphKey graph_key{};
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
-           off_grad = 0, off_ckpt = 0, off_lamb = 0;
+           off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0;
     size_t el = 16;
     size_t ws_bytes = 0;
 
-    DevPlan dev(char* ws, int k0 = 0, int nk = -1) const {
+    DevPlan dev(int k0 = 0, int nk = -1) const {
         DevPlan P{};
         P.N = N;
         P.k0 = k0;
-        P.nk = nk < 0 ? N : nk;
+        P.nk = nk;
         P.nc = nc;
         P.nb = nb;
+        P.n_prob = n_prob;
         P.prec = opts.prec;
         P.dt = dt;
         P.max_sq = opts.max_squarings;
@@ -75,11 +112,14 @@ struct qoc_plan {
         P.blocks = d_blocks;
         P.copy_src = d_copy_src;
         P.copy_base = d_copy_base;
+        P.items = d_items;
+        P.n_items = (long long)items.size();
+        P.prob_blocks = d_prob_blocks;
+        P.prob_block_off = d_prob_block_off;
         P.H = d_H;
         P.H64 = d_H64;
         P.status = d_status;
-        P.stats = profiling ? d_stats : nullptr;
-        (void)ws;
+        P.stats = (profiling && !capturing) ? d_stats : nullptr;
         return P;
     }
 };
@@ -118,22 +158,23 @@ int check_ws(const qoc_plan* p, void* ws, size_t bytes) {
     return QOC_OK;
 }
 
+char* ckpt_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_ckpt + (size_t)i * p->vlen * p->el; }
+char* lamb_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_lamb + (size_t)i * p->vlen * p->el; }
+
+// nk < 0: whole-problem launches over every block; nk >= 0: slice window [k0, k0 + nk) of one problem
 int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
-    const DevPlan P = p->dev(ws, k0, nk);
+    const DevPlan P = p->dev(k0, nk);
     for (const auto& c : p->classes) {
-        if (launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, c.R, ws + p->off_U, ws + p->off_expm,
-                        c.slot_bytes, c.m_max, c.grid, st) != 0)
+        if (launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items, c.R,
+                        ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st) != 0)
             return cuda_fail(cudaGetLastError(), "expm launch");
     }
     return QOC_OK;
 }
 
-char* ckpt_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_ckpt + (size_t)i * p->vlen * p->el; }
-char* lamb_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_lamb + (size_t)i * p->vlen * p->el; }
-
 int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char* fwd_in, char* fwd_out,
                const char* bwd_in, char* bwd_out, cudaStream_t st) {
-    const DevPlan P = p->dev(ws, k0, nk);
+    const DevPlan P = p->dev(k0, nk);
     const int rc = launch_sweeps(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
                                  ws + p->off_lam, dirs, p->max_m, p->max_c, st);
     if (rc == -2) return set_error(QOC_EUNSUPPORTED, "block states do not fit in shared memory");
@@ -142,7 +183,7 @@ int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char
 }
 
 int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
-    const DevPlan P = p->dev(ws, k0, nk);
+    const DevPlan P = p->dev(k0, nk);
     const int g = launch_grad_partials(P, u, ws + p->off_psi, ws + p->off_lam,
                                        reinterpret_cast<double2*>(ws + p->off_partial), ws + p->off_grad,
                                        p->grad_slot, p->max_m, p->grad_grid, st);
@@ -151,17 +192,95 @@ int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
     return QOC_OK;
 }
 
-// Forward pass over all segments: psi_0 (gathered into checkpoint 0) -> checkpoint nseg = psi_N.
+void window_of(const qoc_plan* p, int s, int* k0, int* nk) {
+    *k0 = s * p->seg;
+    *nk = std::min(p->seg, p->N - *k0);
+}
+
+// Forward pass: psi_0 (gathered into checkpoint 0) -> checkpoint nseg = psi_N.
 int forward_pass(const qoc_plan* p, const double* u, const double* psi0, char* w, cudaStream_t st) {
     int rc;
-    if (launch_gather(p->dev(w), reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0)
+    if (launch_gather(p->dev(), reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0)
         return cuda_fail(cudaGetLastError(), "gather launch");
+    if (p->nseg == 1) {
+        if ((rc = run_expm(p, u, w, 0, -1, st))) return rc;
+        return run_sweeps(p, w, 0, -1, 1, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1), nullptr, nullptr, st);
+    }
     for (int s = 0; s < p->nseg; ++s) {
-        const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
+        int k0, nk;
+        window_of(p, s, &k0, &nk);
         if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
         if ((rc = run_sweeps(p, w, k0, nk, 1, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), nullptr, nullptr, st)))
             return rc;
     }
+    return QOC_OK;
+}
+
+UpdateRule no_update() {
+    UpdateRule r{};
+    r.kind = -1;
+    r.f_target = 2.0;
+    return r;
+}
+
+// Phase events: [0]..[1] propagators (and forward sweeps when checkpointing), [1]..[2] sweeps,
+// [2]..[3] overlap, [3]..[4] slice derivatives (with checkpointing: the whole costate pass),
+// [4]..[5] reduction / update.
+int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3,
+                       double* grad, double* u_update, const UpdateRule& rule, char* w, cudaStream_t st) {
+    int rc;
+    const DevPlan P = p->dev();
+    auto mark = [&](int i) {
+        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
+    };
+    const bool want_grad = grad || u_update;
+    double2* o_ws = reinterpret_cast<double2*>(w + p->off_o);
+    mark(0);
+    if (p->nseg == 1) {
+        if (launch_gather(P, reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0 ||
+            (want_grad && launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0))
+            return cuda_fail(cudaGetLastError(), "gather launch");
+        if ((rc = run_expm(p, u, w, 0, -1, st))) return rc;
+        mark(1);
+        if ((rc = run_sweeps(p, w, 0, -1, want_grad ? 3 : 1, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1), lamb_vec(p, w, 0),
+                             lamb_vec(p, w, 1), st)))
+            return rc;
+        mark(2);
+        if (launch_overlap(P, ckpt_vec(p, w, 1), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+            return cuda_fail(cudaGetLastError(), "overlap launch");
+        mark(3);
+        if (want_grad && (rc = run_grad(p, u, w, 0, -1, st))) return rc;
+    } else {
+        if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
+        mark(1);
+        mark(2);
+        if (launch_overlap(P, ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+            return cuda_fail(cudaGetLastError(), "overlap launch");
+        mark(3);
+        if (want_grad) {
+            if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
+                return cuda_fail(cudaGetLastError(), "gather launch");
+            // costate pass: recompute each segment's propagators and states, newest segment first
+            int cur = 0;
+            for (int s = p->nseg - 1; s >= 0; --s) {
+                int k0, nk;
+                window_of(p, s, &k0, &nk);
+                if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
+                if ((rc = run_sweeps(p, w, k0, nk, 3, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), lamb_vec(p, w, cur),
+                                     lamb_vec(p, w, cur ^ 1), st)))
+                    return rc;
+                if ((rc = run_grad(p, u, w, k0, nk, st))) return rc;
+                cur ^= 1;
+            }
+        }
+    }
+    mark(4);
+    if (want_grad) {
+        if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial), o_ws, grad, u_update, rule,
+                               out3, st) != 0)
+            return cuda_fail(cudaGetLastError(), "reduce launch");
+    }
+    mark(5);
     return QOC_OK;
 }
 
@@ -175,102 +294,147 @@ void qoc_plan_opts_default(qoc_plan_opts* o) {
     o->prec = QOC_PREC_F64;
     o->grad_mode = 0;
     o->max_squarings = 16;
+    o->ckpt_segment = 0;
 }
 
-int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* opts, const uint8_t* active,
-                    qoc_plan** out) {
-    if (!B || !out) return set_error(QOC_EINVAL, "null argument");
+void qoc_plan_free(qoc_plan* p);
+
+int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const int* Ns, const double* dts,
+                          const qoc_plan_opts* opts, const uint8_t* const* actives, qoc_plan** out) {
+    if (!bases || !Ns || !dts || !out || n_problems < 1) return set_error(QOC_EINVAL, "null argument or no problem");
     *out = nullptr;
-    if (N < 1) return set_error(QOC_EINVAL, "N must be >= 1");
-    if (!(dt > 0.0) || !std::isfinite(dt)) return set_error(QOC_EINVAL, "dt must be positive and finite");
     qoc_plan_opts o;
     if (opts) o = *opts; else qoc_plan_opts_default(&o);
-    if (o.prec != QOC_PREC_F64 && o.prec != QOC_PREC_F32) return set_error(QOC_EINVAL, "unknown precision");
+    if (o.prec < QOC_PREC_F64 || o.prec > QOC_PREC_F32_ALL) return set_error(QOC_EINVAL, "unknown precision");
     if (o.grad_mode != 0 && o.grad_mode != 1) return set_error(QOC_EINVAL, "unknown grad_mode");
     if (o.max_squarings <= 0) o.max_squarings = 16;
     if (o.max_squarings > 40) return set_error(QOC_EINVAL, "max_squarings must be <= 40");
-    if (B->n_ctrl > 8) return set_error(QOC_EUNSUPPORTED, "at most 8 controls");
+    if (o.ckpt_segment < -1) return set_error(QOC_EINVAL, "ckpt_segment must be -1, 0 or positive");
+    if (o.ckpt_segment != 0 && n_problems > 1) return set_error(QOC_EINVAL, "checkpointing needs a single-problem plan");
+    const int nc = bases[0] ? bases[0]->n_ctrl : 0;
+    for (int i = 0; i < n_problems; ++i) {
+        if (!bases[i]) return set_error(QOC_EINVAL, "null basis");
+        if (bases[i]->n_ctrl != nc) return set_error(QOC_EINVAL, "every problem needs the same number of controls");
+        if (Ns[i] < 1) return set_error(QOC_EINVAL, "N must be >= 1");
+        if (!(dts[i] > 0.0) || !std::isfinite(dts[i])) return set_error(QOC_EINVAL, "dt must be positive and finite");
+    }
+    if (nc < 1 || nc > 8) return set_error(QOC_EUNSUPPORTED, "1..8 controls");
 
     auto* p = new (std::nothrow) qoc_plan();
     if (!p) return set_error(QOC_ENOMEM, "host allocation failed");
-    p->basis = B;
-    p->N = N;
-    p->dt = dt;
     p->opts = o;
-    p->nc = B->n_ctrl;
+    p->nc = nc;
+    p->n_prob = n_problems;
     cudaGetDevice(&p->device);
+    // the FP32 paths store propagators and states in complex FP32
     const size_t el = o.prec == QOC_PREC_F64 ? 16 : 8;
     p->el = el;
-    if (o.ckpt_segment < -1) {
-        delete p;
-        return set_error(QOC_EINVAL, "ckpt_segment must be -1, 0 or positive");
-    }
-    p->seg = o.ckpt_segment == 0 ? N
-             : o.ckpt_segment < 0 ? std::max(1, (int)std::ceil(std::sqrt((double)N)))
-                                  : std::min(o.ckpt_segment, N);
-    p->nseg = (N + p->seg - 1) / p->seg;
+    const int wp = o.prec == QOC_PREC_F64 ? 0 : 1;  // working precision passed to the kernels
 
-    // active blocks, ordered by size (largest first) for load balance
-    struct Act { int b; std::vector<int> copies; };
+    int64_t state_off = 0, u_row = 0;
+    int maxN = 0;
+    for (int i = 0; i < n_problems; ++i) {
+        p->probs.push_back({bases[i], Ns[i], dts[i], state_off, u_row});
+        state_off += bases[i]->state_len;
+        u_row += Ns[i];
+        maxN = std::max(maxN, Ns[i]);
+    }
+    p->rows = u_row;
+    p->state_len = state_off;
+    p->N = maxN;
+    p->dt = dts[0];
+    p->seg = o.ckpt_segment == 0 ? Ns[0]
+             : o.ckpt_segment < 0 ? std::max(1, (int)std::ceil(std::sqrt((double)Ns[0])))
+                                  : std::min(o.ckpt_segment, Ns[0]);
+    p->nseg = n_problems == 1 ? (Ns[0] + p->seg - 1) / p->seg : 1;
+    if (n_problems > 1) p->seg = 0;
+
+    // active blocks of every problem, ordered by size (largest first) for load balance
+    struct Act { int prob; int b; std::vector<int> copies; };
     std::vector<Act> acts;
-    int64_t copy_counter = 0;
-    for (int b = 0; b < (int)B->blocks.size(); ++b) {
-        const auto& blk = B->blocks[b];
-        Act a{b, {}};
-        for (int r = 0; r < blk.c; ++r, ++copy_counter)
-            if (!active || active[copy_counter]) a.copies.push_back(r);
-        if (!a.copies.empty()) acts.push_back(std::move(a));
+    for (int i = 0; i < n_problems; ++i) {
+        const qoc_basis* B = bases[i];
+        int64_t copy_counter = 0;
+        for (int b = 0; b < (int)B->blocks.size(); ++b) {
+            const auto& blk = B->blocks[b];
+            Act a{i, b, {}};
+            for (int r = 0; r < blk.c; ++r, ++copy_counter)
+                if (!actives || !actives[i] || actives[i][copy_counter]) a.copies.push_back(r);
+            if (!a.copies.empty()) acts.push_back(std::move(a));
+        }
     }
     if (acts.empty()) {
         delete p;
         return set_error(QOC_EINVAL, "no active block copy");
     }
-    std::stable_sort(acts.begin(), acts.end(),
-                     [&](const Act& x, const Act& y) { return B->blocks[x.b].m > B->blocks[y.b].m; });
+    std::stable_sort(acts.begin(), acts.end(), [&](const Act& x, const Act& y) {
+        return bases[x.prob]->blocks[x.b].m > bases[y.prob]->blocks[y.b].m;
+    });
     p->nb = (int)acts.size();
 
-    int64_t h_off = 0, u_off = 0, s_off = 0, v_off = 0;
+    int64_t h_off = 0, u_off = 0, s_off = 0, v_off = 0, part_off = 0;
     std::vector<cplx> H64;
-    for (const auto& a : acts) {
-        const auto& blk = B->blocks[a.b];
+    std::vector<std::vector<int>> per_prob(n_problems);
+    for (int bi = 0; bi < p->nb; ++bi) {
+        const auto& a = acts[bi];
+        const auto& pr = p->probs[a.prob];
+        const auto& blk = pr.basis->blocks[a.b];
+        const int slots = p->nseg == 1 ? pr.N : p->seg;
         DevBlock d{};
         d.m = blk.m;
         d.c = (int)a.copies.size();
         d.b = a.b;
+        d.prob = a.prob;
+        d.N = pr.N;
+        d.dt = pr.dt;
+        d.u_row = pr.u_row;
+        d.part_off = part_off;
         d.mmp = ((int64_t)blk.m * blk.m + 3) / 4 * 4;
         d.h_off = h_off;
         d.u_off = u_off;
         d.s_off = s_off;
         d.v_off = v_off;
         d.h0_norm1 = blk.h0_norm1;
-        for (int j = 0; j < p->nc; ++j) d.hc_norm1[j] = blk.hc_norm1[j];
+        for (int j = 0; j < nc; ++j) d.hc_norm1[j] = blk.hc_norm1[j];
         p->copy_base.push_back((int64_t)p->copy_src.size());
-        for (int r : a.copies) p->copy_src.push_back(blk.offset + (int64_t)r * blk.m);
+        for (int r : a.copies) p->copy_src.push_back(pr.state_off + blk.offset + (int64_t)r * blk.m);
         H64.insert(H64.end(), blk.h0.begin(), blk.h0.end());
         H64.insert(H64.end(), blk.hc.begin(), blk.hc.end());
-        h_off += (int64_t)(1 + p->nc) * blk.m * blk.m;
-        u_off += (int64_t)p->seg * d.mmp;
-        s_off += (int64_t)(p->seg + 1) * d.c * d.m;
+        h_off += (int64_t)(1 + nc) * blk.m * blk.m;
+        u_off += (int64_t)slots * d.mmp;
+        s_off += (int64_t)(slots + 1) * d.c * d.m;
         v_off += (int64_t)d.c * d.m;
+        part_off += pr.N;
         p->max_m = std::max(p->max_m, d.m);
         p->max_c = std::max(p->max_c, d.c);
         p->hblocks.push_back(d);
+        per_prob[a.prob].push_back(bi);
+        for (int k = 0; k < pr.N; ++k) p->items.push_back(make_int2(bi, k));
     }
-    // export layout (assemble / expm outputs): active blocks in basis order
+    p->vlen = v_off;
+    p->prob_block_off.push_back(0);
+    for (int i = 0; i < n_problems; ++i) {
+        p->prob_blocks.insert(p->prob_blocks.end(), per_prob[i].begin(), per_prob[i].end());
+        p->prob_block_off.push_back((int)p->prob_blocks.size());
+    }
+    // export layout (assemble / expm outputs): problem by problem, active blocks in basis order
     {
         std::vector<int> order(p->nb);
         for (int i = 0; i < p->nb; ++i) order[i] = i;
-        std::sort(order.begin(), order.end(), [&](int x, int y) { return p->hblocks[x].b < p->hblocks[y].b; });
+        std::sort(order.begin(), order.end(), [&](int x, int y) {
+            const auto& X = p->hblocks[x];
+            const auto& Y = p->hblocks[y];
+            return X.prob != Y.prob ? X.prob < Y.prob : X.b < Y.b;
+        });
         p->a_off.assign(p->nb, 0);
         long long acc = 0;
         for (int i : order) {
             p->a_off[i] = acc;
-            acc += (long long)N * p->hblocks[i].m * p->hblocks[i].m;
+            acc += (long long)p->hblocks[i].N * p->hblocks[i].m * p->hblocks[i].m;
         }
-        p->export_elems = acc;
     }
 
-    // Taylor degree table
+    // Taylor degree table: FP64 unit roundoff for the FP64 path, FP32 otherwise
     const int degs[9] = {2, 4, 6, 9, 12, 16, 20, 25, 30};
     const double unit = o.prec == QOC_PREC_F64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
     for (int i = 0; i < 9; ++i) p->tabs.theta[i] = theta_for(degs[i], unit);
@@ -281,46 +445,51 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
         p->tabs.n_deg = 7;
         p->tabs.theta_cap = std::min(p->tabs.theta[6], 3.0);
     }
+    p->tabs.sq_f64 = o.prec == QOC_PREC_F32_ALL ? 0 : 1;
 
-    // expm size classes
+    // expm size classes: per class, its blocks and its (block, slice) items
     std::vector<int> cls_list;
+    std::vector<int2> cls_items;
     size_t expm_scratch = 0;
     for (int R = 1; R <= 7; ++R) {
-        ExpmClass c{R, (int)cls_list.size(), 0, 0, 0, 0};
+        ExpmClass c{R, (int)cls_list.size(), 0, (long long)cls_items.size(), 0, 0, 0, 0};
         for (int i = 0; i < p->nb; ++i)
-            if (expm_r_for(o.prec, p->hblocks[i].m) == R) {
+            if (expm_r_for(wp, p->hblocks[i].m) == R) {
                 cls_list.push_back(i);
                 c.count++;
                 c.m_max = std::max(c.m_max, p->hblocks[i].m);
+                for (int k = 0; k < p->hblocks[i].N; ++k) cls_items.push_back(make_int2(i, k));
             }
         if (c.count == 0) continue;
-        const long long items = (long long)c.count * p->seg;
-        c.grid = (int)std::min<long long>(items, expm_grid_limit(o.prec, R));
-        c.slot_bytes = align_up(expm_slot_bytes(o.prec, c.m_max), 256);
+        c.n_items = (long long)cls_items.size() - c.item_off;
+        const long long max_items = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
+        c.grid = (int)std::min<long long>(max_items, expm_grid_limit(wp, R));
+        c.slot_bytes = align_up(expm_slot_bytes(wp, c.m_max), 256);
         expm_scratch = std::max(expm_scratch, c.slot_bytes * (size_t)c.grid);
         p->classes.push_back(c);
     }
     // gradient kernel
-    p->grad_slot = align_up(grad_slot_bytes(o.prec, p->max_m), 256);
-    p->grad_grid = (int)std::min<long long>((long long)p->seg * p->nb, grad_grid_limit(o.prec, p->max_m));
-    p->vlen = v_off;
-    if (grad_vector_smem(o.prec, p->max_m) > 220 * 1024) {
-        delete p;
-        return set_error(QOC_EUNSUPPORTED, "block too large for the gradient kernel's shared-memory series");
-    }
+    p->grad_slot = align_up(grad_slot_bytes(wp, p->max_m), 256);
+    const long long grad_items = p->nseg == 1 ? (long long)p->items.size() : (long long)p->seg * p->nb;
+    p->grad_grid = (int)std::min<long long>(grad_items, grad_grid_limit(wp, p->max_m));
 
     // workspace layout
+    const int64_t slot_total = p->nseg == 1 ? 0 : 0;
+    (void)slot_total;
     size_t off = 0;
     p->off_U = off;       off = align_up(off + (size_t)u_off * el, 256);
     p->off_psi = off;     off = align_up(off + (size_t)s_off * el, 256);
     p->off_lam = off;     off = align_up(off + (size_t)s_off * el, 256);
-    p->off_partial = off; off = align_up(off + (size_t)N * p->nb * p->nc * 16, 256);
-    p->off_o = off;       off = align_up(off + 16, 256);
-    p->off_out3 = off;    off = align_up(off + 32, 256);
+    p->off_partial = off; off = align_up(off + (size_t)part_off * nc * 16, 256);
+    p->off_o = off;       off = align_up(off + (size_t)n_problems * 16, 256);
+    p->off_out3 = off;    off = align_up(off + (size_t)n_problems * 24, 256);
     p->off_expm = off;    off = align_up(off + expm_scratch, 256);
     p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
     p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
     p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
+    p->off_adam = off;    off = align_up(off + (size_t)2 * p->rows * nc * sizeof(double), 256);
+    p->off_iter = off;    off = align_up(off + sizeof(int), 256);
+    p->off_reached = off; off = align_up(off + (size_t)n_problems * sizeof(int), 256);
     p->ws_bytes = off;
 
     // device uploads
@@ -330,24 +499,30 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
         return rc;
     };
     cudaError_t e;
-    if ((e = cudaMalloc(&p->d_blocks, sizeof(DevBlock) * p->nb)) != cudaSuccess) return fail(e, "cudaMalloc blocks");
-    if ((e = cudaMalloc(&p->d_copy_src, sizeof(int64_t) * p->copy_src.size())) != cudaSuccess) return fail(e, "cudaMalloc copies");
-    if ((e = cudaMalloc(&p->d_copy_base, sizeof(int64_t) * p->nb)) != cudaSuccess) return fail(e, "cudaMalloc copies");
-    if ((e = cudaMalloc(&p->d_a_off, sizeof(long long) * p->nb)) != cudaSuccess) return fail(e, "cudaMalloc offsets");
-    if ((e = cudaMalloc(&p->d_H64, sizeof(cplx) * H64.size())) != cudaSuccess) return fail(e, "cudaMalloc H");
-    if ((e = cudaMalloc(&p->d_cls, sizeof(int) * std::max<size_t>(1, cls_list.size()))) != cudaSuccess) return fail(e, "cudaMalloc classes");
+#define QOC_UP(dst, src, n, what)                                                             \
+    do {                                                                                      \
+        if ((e = cudaMalloc(&(dst), sizeof(*(src)) * std::max<size_t>(1, (n)))) != cudaSuccess) \
+            return fail(e, what);                                                             \
+        if ((n) > 0 && (e = cudaMemcpy((dst), (src), sizeof(*(src)) * (n), cudaMemcpyHostToDevice)) != cudaSuccess) \
+            return fail(e, what);                                                             \
+    } while (0)
+    QOC_UP(p->d_blocks, p->hblocks.data(), p->hblocks.size(), "upload blocks");
+    QOC_UP(p->d_copy_src, p->copy_src.data(), p->copy_src.size(), "upload copies");
+    QOC_UP(p->d_copy_base, p->copy_base.data(), p->copy_base.size(), "upload copies");
+    QOC_UP(p->d_a_off, p->a_off.data(), p->a_off.size(), "upload offsets");
+    QOC_UP(p->d_cls, cls_list.data(), cls_list.size(), "upload classes");
+    QOC_UP(p->d_cls_items, cls_items.data(), cls_items.size(), "upload class items");
+    QOC_UP(p->d_items, p->items.data(), p->items.size(), "upload items");
+    QOC_UP(p->d_prob_blocks, p->prob_blocks.data(), p->prob_blocks.size(), "upload problems");
+    QOC_UP(p->d_prob_block_off, p->prob_block_off.data(), p->prob_block_off.size(), "upload problems");
+    QOC_UP(p->d_H64, reinterpret_cast<double2*>(H64.data()), H64.size(), "upload H");
+#undef QOC_UP
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc status");
     if ((e = cudaMalloc(&p->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc stats");
     cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
+    cudaMemset(p->d_status, 0, sizeof(int));
     for (auto& ev : p->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e, "cudaEventCreate");
-    cudaMemcpy(p->d_blocks, p->hblocks.data(), sizeof(DevBlock) * p->nb, cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_copy_src, p->copy_src.data(), sizeof(int64_t) * p->copy_src.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_copy_base, p->copy_base.data(), sizeof(int64_t) * p->nb, cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_a_off, p->a_off.data(), sizeof(long long) * p->nb, cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_H64, H64.data(), sizeof(cplx) * H64.size(), cudaMemcpyHostToDevice);
-    cudaMemcpy(p->d_cls, cls_list.data(), sizeof(int) * cls_list.size(), cudaMemcpyHostToDevice);
-    cudaMemset(p->d_status, 0, sizeof(int));
     if (o.prec == QOC_PREC_F64) {
         p->d_H = p->d_H64;
     } else {
@@ -364,6 +539,13 @@ int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* o
     return QOC_OK;
 }
 
+int qoc_plan_create(const qoc_basis* B, int N, double dt, const qoc_plan_opts* opts, const uint8_t* active,
+                    qoc_plan** out) {
+    if (!B) return set_error(QOC_EINVAL, "null basis");
+    const uint8_t* acts[1] = {active};
+    return qoc_plan_create_batch(&B, 1, &N, &dt, opts, acts, out);
+}
+
 void qoc_plan_free(qoc_plan* p) {
     if (!p) return;
     cudaFree(p->d_blocks);
@@ -373,11 +555,24 @@ void qoc_plan_free(qoc_plan* p) {
     if (p->d_H && p->d_H != p->d_H64) cudaFree(p->d_H);
     cudaFree(p->d_H64);
     cudaFree(p->d_cls);
+    cudaFree(p->d_cls_items);
+    cudaFree(p->d_items);
+    cudaFree(p->d_prob_blocks);
+    cudaFree(p->d_prob_block_off);
     cudaFree(p->d_status);
     cudaFree(p->d_stats);
     for (auto& ev : p->ev)
         if (ev) cudaEventDestroy(ev);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
     delete p;
+}
+
+int qoc_plan_info(const qoc_plan* p, int* n_problems, int64_t* pulse_rows, int64_t* state_len) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    if (n_problems) *n_problems = p->n_prob;
+    if (pulse_rows) *pulse_rows = p->rows;
+    if (state_len) *state_len = p->state_len;
+    return QOC_OK;
 }
 
 int qoc_plan_workspace_bytes(const qoc_plan* p, size_t* bytes) {
@@ -437,11 +632,11 @@ int qoc_plan_work_counts(qoc_plan* p, long long* out, int n) {
 
 int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     if (!p || !launches) return set_error(QOC_EINVAL, "null argument");
-    // expm: one launch per size class; then sweeps, overlap, slice derivatives, reduction
-    // (propagate: sweeps and the final-state store after a memset)
+    // gathers, one expm launch per size class, sweeps, overlap, slice derivatives, reduction
+    // (+ the iteration counter when optimising); propagate: gather, expm, sweep, memset, store
     const int ncls = (int)p->classes.size();
     if (p->nseg == 1)
-        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + 1 : 1 + ncls + 1 + 1;  // gathers, expm, sweeps, overlap, grad, reduce
+        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + 1 : 1 + ncls + 1 + 1;
     else
         *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (ncls + 2) + 1
                               : 1 + p->nseg * (ncls + 1) + 1;
@@ -451,8 +646,7 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
 int qoc_assemble_blocks(const qoc_plan* p, const double* u, double* A_out, void* stream) {
     if (!p || !u || !A_out) return set_error(QOC_EINVAL, "null argument");
     cudaSetDevice(p->device);
-    const DevPlan P = p->dev(nullptr);
-    if (launch_assemble(P, u, reinterpret_cast<double2*>(A_out), p->d_a_off, to_stream(stream)) != 0)
+    if (launch_assemble(p->dev(), u, reinterpret_cast<double2*>(A_out), p->d_a_off, to_stream(stream)) != 0)
         return cuda_fail(cudaGetLastError(), "assemble launch");
     return QOC_OK;
 }
@@ -464,10 +658,17 @@ int qoc_expm_blocks(const qoc_plan* p, const double* u, double* U_out, void* ws,
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
+    if (p->nseg == 1) {
+        if ((rc = run_expm(p, u, w, 0, -1, st))) return rc;
+        if (launch_export_u(p->dev(), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
+            return cuda_fail(cudaGetLastError(), "export launch");
+        return QOC_OK;
+    }
     for (int s = 0; s < p->nseg; ++s) {
-        const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
+        int k0, nk;
+        window_of(p, s, &k0, &nk);
         if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
-        if (launch_export_u(p->dev(w, k0, nk), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
+        if (launch_export_u(p->dev(k0, nk), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
             return cuda_fail(cudaGetLastError(), "export launch");
     }
     return QOC_OK;
@@ -482,70 +683,8 @@ int qoc_propagate(const qoc_plan* p, const double* u, const double* psi0, double
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
     if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
-    if (launch_store_final(p->dev(w), ckpt_vec(p, w, p->nseg), reinterpret_cast<double2*>(psiN), p->basis->state_len,
-                           st) != 0)
+    if (launch_store_final(p->dev(), ckpt_vec(p, w, p->nseg), reinterpret_cast<double2*>(psiN), p->state_len, st) != 0)
         return cuda_fail(cudaGetLastError(), "store launch");
-    return QOC_OK;
-}
-
-// Phase events: [0]..[1] propagators (+ forward sweeps when checkpointing), [1]..[2] sweeps (costate
-// pass when checkpointing: recomputed propagators, both sweeps and slice derivatives), [2]..[3]
-// overlap, [3]..[4] slice derivatives (0 when checkpointing), [4]..[5] reduction / update.
-static int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif,
-                              double* out3, double* grad, double* u_update, double step, double* F_slot, char* w,
-                              cudaStream_t st) {
-    int rc;
-    const DevPlan P = p->dev(w);
-    auto mark = [&](int i) {
-        if (p->profiling) cudaEventRecord(p->ev[i], st);
-    };
-    const bool want_grad = grad || u_update;
-    double2* o_ws = reinterpret_cast<double2*>(w + p->off_o);
-    mark(0);
-    if (p->nseg == 1) {
-        if (launch_gather(P, reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0 ||
-            (want_grad && launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0))
-            return cuda_fail(cudaGetLastError(), "gather launch");
-        if ((rc = run_expm(p, u, w, 0, p->N, st))) return rc;
-        mark(1);
-        if ((rc = run_sweeps(p, w, 0, p->N, want_grad ? 3 : 1, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1),
-                             lamb_vec(p, w, 0), lamb_vec(p, w, 1), st)))
-            return rc;
-        mark(2);
-        if (launch_overlap(P, ckpt_vec(p, w, 1), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
-            return cuda_fail(cudaGetLastError(), "overlap launch");
-        mark(3);
-        if (want_grad && (rc = run_grad(p, u, w, 0, p->N, st))) return rc;
-    } else {
-        if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
-        mark(1);
-        if (launch_overlap(P, ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
-            return cuda_fail(cudaGetLastError(), "overlap launch");
-        mark(2);
-        if (want_grad) {
-            if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
-                return cuda_fail(cudaGetLastError(), "gather launch");
-            // costate pass: recompute each segment's propagators and states, newest segment first
-            int cur = 0;
-            for (int s = p->nseg - 1; s >= 0; --s) {
-                const int k0 = s * p->seg, nk = std::min(p->seg, p->N - k0);
-                if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
-                if ((rc = run_sweeps(p, w, k0, nk, 3, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), lamb_vec(p, w, cur),
-                                     lamb_vec(p, w, cur ^ 1), st)))
-                    return rc;
-                if ((rc = run_grad(p, u, w, k0, nk, st))) return rc;
-                cur ^= 1;
-            }
-        }
-        mark(3);
-    }
-    mark(4);
-    if (want_grad) {
-        if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial), o_ws, grad, u_update, step,
-                               F_slot, out3, st) != 0)
-            return cuda_fail(cudaGetLastError(), "reduce launch");
-    }
-    mark(5);
     return QOC_OK;
 }
 
@@ -555,44 +694,124 @@ int qoc_fidelity_and_grad(const qoc_plan* p, const double* u, const double* psi0
     int rc = check_ws(p, ws, ws_bytes);
     if (rc) return rc;
     cudaSetDevice(p->device);
-    return fidelity_grad_impl(p, u, psi0, psif, out3, grad, nullptr, 0.0, nullptr, static_cast<char*>(ws),
+    return fidelity_grad_impl(p, u, psi0, psif, out3, grad, nullptr, no_update(), static_cast<char*>(ws),
                               to_stream(stream));
 }
 
-int qoc_optimize_pulses(const qoc_plan* p, double* u, const double* psi0, const double* psif, int iters, double step,
-                        double f_target, int check_every, double* F_hist, int* iters_done, void* ws, size_t ws_bytes,
-                        void* stream) {
-    if (!p || !u || !psi0 || !psif || !F_hist) return set_error(QOC_EINVAL, "null argument");
-    if (iters < 0) return set_error(QOC_EINVAL, "iters must be >= 0");
-    if (!std::isfinite(step)) return set_error(QOC_EINVAL, "step must be finite");
+void qoc_opt_opts_default(qoc_opt_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->iters = 100;
+    o->rule = QOC_RULE_FIXED;
+    o->step = 0.1;
+    o->beta1 = 0.9;
+    o->beta2 = 0.999;
+    o->eps = 1e-8;
+    o->f_target = 2.0;
+    o->check_every = 10;
+    o->use_graph = 0;
+    o->freeze_converged = 1;
+}
+
+int qoc_optimize_pulses(qoc_plan* p, double* u, const double* psi0, const double* psif, const qoc_opt_opts* oo,
+                        double* F_hist, int* reached, int* iters_done, void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !u || !psi0 || !psif || !F_hist || !oo) return set_error(QOC_EINVAL, "null argument");
+    const qoc_opt_opts o = *oo;
+    if (o.iters < 0) return set_error(QOC_EINVAL, "iters must be >= 0");
+    if (o.rule != QOC_RULE_FIXED && o.rule != QOC_RULE_ADAM) return set_error(QOC_EINVAL, "unknown update rule");
+    if (!std::isfinite(o.step)) return set_error(QOC_EINVAL, "step must be finite");
     int rc = check_ws(p, ws, ws_bytes);
     if (rc) return rc;
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
+    if (o.use_graph && st == nullptr) return set_error(QOC_EINVAL, "graph replay needs a non-default stream");
     double* out3 = reinterpret_cast<double*>(w + p->off_out3);
-    const bool stop_early = f_target <= 1.0;
-    if (check_every < 1) check_every = 1;
+    int* d_iter = reinterpret_cast<int*>(w + p->off_iter);
+    int* d_reached = reached ? reached : reinterpret_cast<int*>(w + p->off_reached);
+    UpdateRule rule{};
+    rule.kind = o.rule;
+    rule.freeze = o.freeze_converged && o.f_target <= 1.0;
+    rule.step = o.step;
+    rule.beta1 = o.beta1;
+    rule.beta2 = o.beta2;
+    rule.eps = o.eps;
+    rule.f_target = o.f_target;
+    rule.iter = d_iter;
+    rule.reached = d_reached;
+    rule.adam_m = reinterpret_cast<double*>(w + p->off_adam);
+    rule.adam_v = rule.adam_m + p->rows * p->nc;
+    rule.F_hist = F_hist;
+    // fresh optimiser state
+    cudaMemsetAsync(d_iter, 0, sizeof(int), st);
+    cudaMemsetAsync(d_reached, 0xFF, sizeof(int) * p->n_prob, st);
+    cudaMemsetAsync(rule.adam_m, 0, sizeof(double) * 2 * p->rows * p->nc, st);
+
+    const bool stop_early = o.f_target <= 1.0;
+    const int check_every = o.check_every < 1 ? 1 : o.check_every;
+    std::vector<int> h_reached(p->n_prob);
+    auto all_reached = [&](bool* all) -> int {
+        cudaError_t e = cudaMemcpyAsync(h_reached.data(), d_reached, sizeof(int) * p->n_prob, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "convergence read");
+        *all = true;
+        for (int v : h_reached)
+            if (v < 0) *all = false;
+        return QOC_OK;
+    };
+
+    if (o.use_graph) {
+        GraphKey key{};
+        key.u = u; key.psi0 = psi0; key.psif = psif; key.F_hist = F_hist; key.reached = d_reached; key.ws = ws;
+        key.step = o.step; key.beta1 = o.beta1; key.beta2 = o.beta2; key.eps = o.eps; key.f_target = o.f_target;
+        key.kind = rule.kind; key.freeze = rule.freeze; key.stream = st;
+        if (!p->graph || std::memcmp(&key, &p->graph_key, sizeof(GraphKey)) != 0) {
+            if (p->graph) {
+                cudaGraphExecDestroy(p->graph);
+                p->graph = nullptr;
+            }
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) return cuda_fail(e, "begin capture");
+            p->capturing = true;
+            rc = fidelity_grad_impl(p, u, psi0, psif, out3, nullptr, u, rule, w, st);
+            p->capturing = false;
+            e = cudaStreamEndCapture(st, &g);
+            if (rc) {
+                if (g) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return cuda_fail(e, "end capture");
+            e = cudaGraphInstantiate(&p->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                p->graph = nullptr;
+                return cuda_fail(e, "graph instantiate");
+            }
+            p->graph_key = key;
+        }
+    }
     int done = 0;
-    for (int it = 0; it < iters; ++it) {
-        double* trip = F_hist + it;  // F at the current pulses, copied here by the reduction kernel
-        rc = fidelity_grad_impl(p, u, psi0, psif, out3, nullptr, u, step, trip, w, st);
-        if (rc) return rc;
+    for (int it = 0; it < o.iters; ++it) {
+        if (o.use_graph) {
+            cudaError_t e = cudaGraphLaunch(p->graph, st);
+            if (e != cudaSuccess) return cuda_fail(e, "graph launch");
+        } else {
+            rc = fidelity_grad_impl(p, u, psi0, psif, out3, nullptr, u, rule, w, st);
+            if (rc) return rc;
+        }
         done = it + 1;
         if (stop_early && (done % check_every == 0)) {
-            double F = 0.0;
-            cudaError_t e = cudaMemcpyAsync(&F, trip, sizeof(double), cudaMemcpyDeviceToHost, st);
-            if (e == cudaSuccess) e = cudaStreamSynchronize(st);
-            if (e != cudaSuccess) return cuda_fail(e, "fidelity read");
-            if (F >= f_target) break;
+            bool all = false;
+            if ((rc = all_reached(&all))) return rc;
+            if (all) break;
         }
     }
     if (iters_done) *iters_done = done;
-    if (stop_early && done > 0) {
-        double F = 0.0;
-        cudaMemcpyAsync(&F, F_hist + done - 1, sizeof(double), cudaMemcpyDeviceToHost, st);
-        cudaStreamSynchronize(st);
-        if (!(F >= f_target)) return set_error(QOC_ENOTCONVERGED, "F_target not reached");
+    if (stop_early) {
+        bool all = false;
+        if ((rc = all_reached(&all))) return rc;
+        if (!all) return set_error(QOC_ENOTCONVERGED, "F_target not reached by every problem");
     }
     return QOC_OK;
 }

@@ -33,7 +33,7 @@ sweep_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __restrict__ f
     const bool fwd = (int)blockIdx.x < nfw;
     const int bi = fwd ? (int)blockIdx.x : (int)blockIdx.x - nfw;
     const DevBlock B = P.blocks[bi];
-    const int m = B.m, c = B.c, NK = P.nk;
+    const int m = B.m, c = B.c, NK = P.nk < 0 ? B.N : P.nk;
     const long long mmp = B.mmp;
     const uint32_t ubytes = (uint32_t)(mmp * (long long)sizeof(cx<T>));
     cx<T>* ubuf0 = reinterpret_cast<cx<T>*>(dsm);
@@ -138,13 +138,17 @@ __global__ void gather_kernel(DevPlan P, const double2* __restrict__ src, cx<T>*
     }
 }
 
+// One CTA per problem: o_p = sum over the problem's active copies <psif|psi_N> in FP64;
+// out3[3p..3p+2] = {|o_p|^2, Re o_p, Im o_p}; o_ws[p] = o_p.
 template <class T>
 __global__ void __launch_bounds__(256)
 overlap_kernel(DevPlan P, const cx<T>* __restrict__ fin, const double2* __restrict__ psif, double* out3,
                double2* o_ws) {
     __shared__ double sre[256], sim[256];
+    const int p = blockIdx.x;
     double re = 0.0, im = 0.0;
-    for (int bi = 0; bi < P.nb; ++bi) {
+    for (int t = P.prob_block_off[p]; t < P.prob_block_off[p + 1]; ++t) {
+        const int bi = P.prob_blocks[t];
         const DevBlock& B = P.blocks[bi];
         const int m = B.m, c = B.c;
         const long long cb = P.copy_base[bi];
@@ -169,11 +173,11 @@ overlap_kernel(DevPlan P, const cx<T>* __restrict__ fin, const double2* __restri
     }
     if (threadIdx.x == 0) {
         const double a = sre[0], b = sim[0];
-        out3[0] = a * a + b * b;
-        out3[1] = a;
-        out3[2] = b;
-        o_ws->x = a;
-        o_ws->y = b;
+        out3[3 * p + 0] = a * a + b * b;
+        out3[3 * p + 1] = a;
+        out3[3 * p + 2] = b;
+        o_ws[p].x = a;
+        o_ws[p].y = b;
     }
 }
 
@@ -235,9 +239,9 @@ int launch_gather(const DevPlan& P, const double2* src, void* dst, cudaStream_t 
 int launch_overlap(const DevPlan& P, const void* fin, const double2* psif, double* out3, double2* o_ws,
                    cudaStream_t st) {
     if (P.prec == 0)
-        overlap_kernel<double><<<1, 256, 0, st>>>(P, (const double2*)fin, psif, out3, o_ws);
+        overlap_kernel<double><<<P.n_prob, 256, 0, st>>>(P, (const double2*)fin, psif, out3, o_ws);
     else
-        overlap_kernel<float><<<1, 256, 0, st>>>(P, (const float2*)fin, psif, out3, o_ws);
+        overlap_kernel<float><<<P.n_prob, 256, 0, st>>>(P, (const float2*)fin, psif, out3, o_ws);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

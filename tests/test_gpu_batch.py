@@ -1,0 +1,113 @@
+"""Batched many-problem GRAPE: independent S_n problems of different n, N and tau in one plan (every
+launch covers all of them), against the oracle problem by problem; sub-stepped slices of large
+norm; Adam ascent with CUDA-graph replay against the oracle's trajectory."""
+import numpy as np
+import pytest
+
+from oracle import grape as gr
+from oracle import symmetry as sy
+from paper_2309_05884_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2309_05884_gb300 import api  # noqa: E402
+
+DEV = torch.device("cuda", 0)
+
+
+def oracle_block(n, J, h, k):
+    """The oracle's own J = n/2 block of J sum_{i<j} Z_i Z_j + h sum Z_i with controls sum X, sum Y."""
+    Jz, Jp, Jm = sy.spin_matrices(n)
+    m = n + 1
+    p0 = np.zeros((m, 1), complex)
+    p0[0] = 1
+    pf = np.zeros((m, 1), complex)
+    pf[k] = 1
+    return [dict(h0=J * (2 * Jz @ Jz - n / 2 * np.eye(m)) + h * 2 * Jz, hc=[Jp + Jm, -1j * (Jp - Jm)],
+                 psi0=p0, psif=pf)]
+
+
+def make_batch(probs, T, prec, init="uniform"):
+    systems = [I.sn_allpairs(p.n, p.J, p.h, T, p.N) for p in probs]
+    bases = [api.Basis(s, first_block_only=True, vectors=False) for s in systems]
+    psi0 = np.concatenate([b.dicke_state(0) for b in bases])
+    psif = np.concatenate([b.dicke_state(p.k_target) for b, p in zip(bases, probs)])
+    us = [I.pulses_uniform(p.seed, p.N, 2) for p in probs]
+    plan = api.Plan(bases, [p.N for p in probs], [T / p.N for p in probs], prec=prec)
+    return plan, systems, api.to_device(psi0, DEV), api.to_device(psif, DEV), us
+
+
+def run(plan, u, d0, df):
+    out3, g = plan.fidelity_and_grad(torch.from_numpy(u).to(DEV), d0, df)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    return out3.cpu().numpy().reshape(-1, 3), g.cpu().numpy()
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32_all", 1e-5), ("f32", 1e-5)])
+def test_batch_matches_oracle_per_problem(prec, tol):
+    probs = I.sn_problem_batch(7, base_seed=20_000, n_lo=3, n_hi=14, N_lo=15, N_hi=60)
+    T = 1.0
+    plan, systems, d0, df, us = make_batch(probs, T, prec)
+    assert plan.n_prob == 7 and plan.rows == sum(p.N for p in probs)
+    out, g = run(plan, np.concatenate(us), d0, df)
+    row = 0
+    for i, p in enumerate(probs):
+        F, o, gref = gr.fidelity_and_grad(oracle_block(p.n, p.J, p.h, p.k_target), us[i], T / p.N)
+        gi = g[row: row + p.N]
+        row += p.N
+        assert abs(out[i, 0] - F) <= tol
+        if np.linalg.norm(gref) > 1e-8:
+            assert np.linalg.norm(gi - gref) / np.linalg.norm(gref) <= tol, (i, p)
+
+
+def test_batch_equals_individual_plans():
+    probs = I.sn_problem_batch(5, base_seed=21_000, n_lo=4, n_hi=20, N_lo=10, N_hi=40)
+    plan, systems, d0, df, us = make_batch(probs, 1.0, "f32_all")
+    out, g = run(plan, np.concatenate(us), d0, df)
+    row = 0
+    for i, p in enumerate(probs):
+        pl, _, a0, af, _ = make_batch([p], 1.0, "f32_all")
+        o1, g1 = run(pl, us[i], a0, af)
+        assert np.array_equal(o1[0], out[i]) and np.array_equal(g1, g[row: row + p.N])
+        row += p.N
+
+
+@pytest.mark.parametrize("prec,tol", [("f64", 1e-10), ("f32_all", 1e-5)])
+def test_large_norm_slices_are_sub_stepped(prec, tol):
+    # n = 24, J = 2: |tau H0| ~ 10-20 per slice -> 2^2..2^3 sub-slices in the gradient
+    p = I.SnProblem(n=24, J=2.0, h=0.7, N=40, k_target=3, seed=77)
+    T = 1.0
+    plan, systems, d0, df, us = make_batch([p], T, prec)
+    out, g = run(plan, us[0], d0, df)
+    F, o, gref = gr.fidelity_and_grad(oracle_block(p.n, p.J, p.h, p.k_target), us[0], T / p.N)
+    assert abs(out[0, 0] - F) <= tol
+    assert np.linalg.norm(g - gref) / np.linalg.norm(gref) <= tol
+
+
+def test_batched_adam_graph_replay_matches_oracle():
+    probs = I.sn_problem_batch(4, base_seed=22_000, n_lo=3, n_hi=8, N_lo=20, N_hi=40)
+    T, iters, lr, ft = 1.0, 60, 0.2, 0.95
+    plan, systems, d0, df, us = make_batch(probs, T, "f64")
+    u_graph = torch.from_numpy(np.concatenate(us)).to(DEV)
+    u_plain = u_graph.clone()
+    Fg, done_g, _ = plan.optimize(u_graph, d0, df, iters, lr, f_target=ft, check_every=iters, rule="adam",
+                                  use_graph=True)
+    reached_g = plan.last_reached.cpu().numpy()
+    Fp, done_p, _ = plan.optimize(u_plain, d0, df, iters, lr, f_target=ft, check_every=iters, rule="adam")
+    torch.cuda.synchronize()
+    assert done_g == done_p == iters
+    assert torch.equal(u_graph, u_plain) and torch.equal(Fg, Fp)
+    row = 0
+    for i, p in enumerate(probs):
+        ur, hist, reached = gr.grape_adam(oracle_block(p.n, p.J, p.h, p.k_target), us[i], T / p.N, iters, lr,
+                                          f_target=ft)
+        assert reached_g[i] == reached
+        assert np.abs(u_graph.cpu().numpy()[row: row + p.N] - ur).max() <= 1e-8
+        n_hist = len(hist)
+        assert np.abs(Fg.cpu().numpy()[:n_hist, i] - np.array(hist)).max() <= 1e-9
+        row += p.N

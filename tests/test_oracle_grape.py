@@ -171,3 +171,30 @@ def test_grape_invariance_full_vs_block():
     ub, hb, _ = gr.grape(block_problem(s, *c1_states()), u0, s.tau, 200, 0.2)
     assert np.abs(uf - ub).max() < 1e-10
     assert hf[-1] > hf[0]
+
+
+def test_adam_first_step_is_signed_step():
+    # with zero moments, the first Adam step moves every coordinate by step * sign(g) (up to eps)
+    g = np.array([[0.3, -2.0], [1e-3, 5.0]])
+    u, m, v = gr.adam_update(np.zeros_like(g), g, np.zeros_like(g), np.zeros_like(g), 1, 0.1)
+    assert np.allclose(u, 0.1 * np.sign(g), atol=1e-6)
+    # and the second step with the same gradient again moves by step * sign(g)
+    u2, _, _ = gr.adam_update(u, g, m, v, 2, 0.1)
+    assert np.allclose(u2 - u, 0.1 * np.sign(g), atol=1e-6)
+
+
+def test_grape_adam_escapes_tiny_overlap():
+    # |0...0> -> D(6, 3) with weak random pulses: F starts near 0, fixed steps barely move, Adam
+    # (scale-free steps) reaches F >= 0.999
+    n, N, T = 6, 60, 1.0
+    Jz, Jp, Jm = sy.spin_matrices(n)
+    m = n + 1
+    p0 = np.zeros((m, 1), complex)
+    p0[0] = 1
+    pf = np.zeros((m, 1), complex)
+    pf[3] = 1
+    prob = [dict(h0=0.8 * (2 * Jz @ Jz - n / 2 * np.eye(m)) + 0.4 * 2 * Jz, hc=[Jp + Jm, -1j * (Jp - Jm)],
+                 psi0=p0, psif=pf)]
+    u0 = I.pulses_uniform(1, N, 2, -0.1, 0.1)
+    _, hist, reached = gr.grape_adam(prob, u0, T / N, 2000, 0.5, f_target=0.999)
+    assert hist[0] < 1e-3 and reached >= 0 and hist[-1] >= 0.999
