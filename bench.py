@@ -49,6 +49,17 @@ def workload():
     return s, psi0, psif, u
 
 
+SN_BATCH = 256
+SN_T = 10.0
+SN_WORKLOAD = (f"{SN_BATCH} independent S_n problems (H0 = J sum_{{i<j}} Z_i Z_j + h sum Z_i, controls sum X, sum Y), "
+               f"n ~ U{{8..64}}, J ~ U[0.5,2], h ~ U[0,1], N ~ U{{200..1000}}, T = {SN_T}, |0...0> -> Dicke "
+               f"D(n,k), k ~ U{{0..n}}, pulses U[-1,1], seeds 10000+i; block J = n/2 (size n+1) per problem")
+
+
+def sn_batch_problems():
+    return I.sn_problem_batch(SN_BATCH, base_seed=10_000)
+
+
 # --------------------------------------------------------------------------- clocks
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -162,6 +173,70 @@ def run_reference(args, rank, world):
     }), flush=True)
 
 
+# --------------------------------------------------------------------------- workloads
+class D10:
+    """The D_10 XXZ ring, all irrep blocks (default)."""
+    name = WORKLOAD
+    problems = 1
+    prec = "f32"
+    step_kw = dict(step=EPS, rule="fixed")
+
+    def build(self, api, dev):
+        s, psi0_full, psif_full, u0 = workload()
+        B = api.Basis(s)
+        b0, bf = B.state_to_blocks(psi0_full), B.state_to_blocks(psif_full)
+        plan = api.Plan(B, s.N, s.tau, prec=self.prec, active=B.active_copies(b0, bf))
+        self._s, self._p0, self._pf, self._u = s, psi0_full, psif_full, u0
+        return plan, u0, b0, bf
+
+    def cpu_rate(self):
+        Ns = 250
+        rate, secs = cpu_oracle_rate(self._s, self._p0, self._pf, self._u, Ns)
+        return rate, (f"one FP64 oracle F + exact gradient over the first {Ns} of {self._s.N} slices "
+                      f"(all blocks, numpy/BLAS default threads), {secs:.1f} s, scaled by {Ns}/{self._s.N}")
+
+
+class SnBatch:
+    """256 independent S_n problems per launch (batched many-problem solve)."""
+    name = SN_WORKLOAD
+    problems = SN_BATCH
+    prec = "f32_all"
+    step_kw = dict(step=0.02, rule="fixed")
+
+    def build(self, api, dev):
+        probs = sn_batch_problems()
+        self._probs = probs
+        systems = [I.sn_allpairs(p.n, p.J, p.h, SN_T, p.N) for p in probs]
+        bases = [api.Basis(s, first_block_only=True, vectors=False) for s in systems]
+        b0 = np.concatenate([bb.dicke_state(0) for bb in bases])
+        bf = np.concatenate([bb.dicke_state(p.k_target) for bb, p in zip(bases, probs)])
+        u0 = np.concatenate([I.pulses_uniform(p.seed, p.N, 2) for p in probs])
+        plan = api.Plan(bases, [p.N for p in probs], [SN_T / p.N for p in probs], prec=self.prec)
+        return plan, u0, b0, bf
+
+    def cpu_rate(self):
+        from oracle import grape as gr
+        from oracle import symmetry as sy
+        sample = self._probs[:8]
+        t0 = time.perf_counter()
+        for p in sample:
+            Jz, Jp, Jm = sy.spin_matrices(p.n)
+            m = p.n + 1
+            p0 = np.zeros((m, 1), complex)
+            p0[0] = 1
+            pf = np.zeros((m, 1), complex)
+            pf[p.k_target] = 1
+            prob = [dict(h0=p.J * (2 * Jz @ Jz - p.n / 2 * np.eye(m)) + p.h * 2 * Jz, hc=[Jp + Jm, -1j * (Jp - Jm)],
+                         psi0=p0, psif=pf)]
+            gr.fidelity_and_grad(prob, I.pulses_uniform(p.seed, p.N, 2), SN_T / p.N)
+        secs = time.perf_counter() - t0
+        return len(sample) / secs, (f"FP64 oracle F + exact gradient of the first {len(sample)} of the "
+                                    f"{SN_BATCH} problems ({secs:.1f} s), problems per second")
+
+
+WORKLOADS = {"d10": D10, "sn-batch": SnBatch}
+
+
 # --------------------------------------------------------------------------- GPU leg
 def run_ours(args, rank, world):
     import torch
@@ -170,10 +245,12 @@ def run_ours(args, rank, world):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    s, psi0_full, psif_full, u0 = workload()
-    B = api.Basis(s)
-    b0, bf = B.state_to_blocks(psi0_full), B.state_to_blocks(psif_full)
-    plan = api.Plan(B, s.N, s.tau, prec="f32", active=B.active_copies(b0, bf))
+    wl = WORKLOADS[args.workload]()
+    plan, u0, b0, bf = wl.build(api, dev)
+    if args.autotune:
+        from paper_2309_05884_gb300 import autotune
+        autotune.tune_expm(plan, torch.from_numpy(u0).to(dev), api.to_device(b0, dev), api.to_device(bf, dev),
+                           cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json"))
     d0, df = api.to_device(b0, dev), api.to_device(bf, dev)
     u = torch.from_numpy(u0.copy()).to(dev)
     ws = plan.workspace  # allocate before timing
@@ -181,7 +258,7 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
 
     def step():
-        plan.optimize(u, d0, df, iters=1, step=EPS)
+        plan.optimize(u, d0, df, iters=1, **wl.step_kw)
 
     for _ in range(args.warmup):
         step()
@@ -218,31 +295,33 @@ def run_ours(args, rank, world):
         t = torch.tensor([total_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1e3)
+    value = world * wl.problems * args.steps / (total_ms / 1e3)
     ph = np.mean(np.array(phases), axis=0)
 
-    # roofline of the dominant kernel (the batched expm): algorithmic flops per launch set
-    flops_poly = 8.0 * counts[0] / args.steps       # complex MAC = 8 real flops
+    # roofline of the batched exponential: algorithmic flops per launch set (complex MAC = 8 flop)
+    flops_poly = 8.0 * counts[0] / args.steps
     flops_sq = 8.0 * counts[1] / args.steps
     expm_ms = float(ph[0])
     achieved = (flops_poly + flops_sq) / (expm_ms * 1e-3) / 1e12
-    roof = {"bound": "alu", "kernel": "expm_kernel (all size classes of one call)",
+    phase_ms = {"expm": float(ph[0]), "sweeps": float(ph[1]), "overlap": float(ph[2]),
+                "slice_derivatives": float(ph[3]), "reduce_update": float(ph[4])}
+    roof = {"bound": "alu", "kernel": "batched expm (all launches of one call)",
             "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
             "traffic": None, "peak_source": FP32_PEAK_NOTE,
-            "flops_per_launch": flops_poly + flops_sq, "fp64_squaring_flops": flops_sq,
-            "phase_ms": {"expm": float(ph[0]), "sweeps": float(ph[1]), "overlap": float(ph[2]),
-                         "slice_derivatives": float(ph[3]), "reduce_update": float(ph[4])}}
+            "flops_per_launch": flops_poly + flops_sq, "squaring_flops": flops_sq, "phase_ms": phase_ms,
+            "dominant_phase": max(phase_ms, key=phase_ms.get)}
 
     # end to end through the C ABI with host buffers: H2D of u and both states, D2H of F and dF/du
     u_h = torch.from_numpy(u0.copy()).pin_memory()
     b0_h = torch.from_numpy(b0).pin_memory()
     bf_h = torch.from_numpy(bf).pin_memory()
-    out_h = torch.empty(3, dtype=torch.float64).pin_memory()
+    out_h = torch.empty(3 * plan.n_prob, dtype=torch.float64).pin_memory()
     g_h = torch.empty_like(u_h).pin_memory()
     u_d, d0e, dfe = torch.empty_like(u), torch.empty_like(d0), torch.empty_like(df)
-    out3 = torch.empty(3, dtype=torch.float64, device=dev)
+    out3 = torch.empty(3 * plan.n_prob, dtype=torch.float64, device=dev)
     gd = torch.empty_like(u)
     e2e_steps = max(3, args.steps // 2)
+    lr = wl.step_kw["step"]
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -254,33 +333,33 @@ def run_ours(args, rank, world):
         out_h.copy_(out3, non_blocking=True)
         g_h.copy_(gd, non_blocking=True)
         torch.cuda.synchronize()
-        u_h += EPS * g_h
+        u_h += lr * g_h
     e2e_s = time.perf_counter() - t0
     h2d = u_h.numel() * 8 + b0_h.numel() * 16 + bf_h.numel() * 16
-    d2h = 3 * 8 + g_h.numel() * 8
+    d2h = out_h.numel() * 8 + g_h.numel() * 8
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Ns = 250
-        rate, secs = cpu_oracle_rate(s, psi0_full, psif_full, u0, Ns)
-        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"one FP64 oracle F + exact gradient over the first {Ns} of {s.N} slices "
-                         f"(all blocks, numpy/BLAS default threads), {secs:.1f} s, scaled by {Ns}/{s.N}"}
+        rate, sample = wl.cpu_rate()
+        cpu = {"value": rate, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": sample}
 
     if rank == 0:
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "precision": "complex FP32 polynomial + sweeps; FP64 squaring, "
-                                                          "overlap, gradient accumulation",
-                       "problems_per_step": 1, "l2": "flushed between timed steps (256 MB write)",
+            "config": {"workload": wl.name, "precision": {"f32": "complex FP32 polynomial + sweeps; FP64 squaring, "
+                                                                  "overlap, gradient accumulation",
+                                                           "f32_all": "complex FP32 polynomial, squaring and sweeps; "
+                                                                      "FP64 overlap and gradient accumulation"}[wl.prec],
+                       "problems_per_step": wl.problems, "l2": "flushed between timed steps (256 MB write)",
+                       "expm_kernels": [list(c) for c in plan.expm_classes()],
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
             "cpu_baseline": cpu,
-            "e2e": {"value": world * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "e2e": {"value": world * wl.problems * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
-            "gpu_launches": plan.kernel_launches(True) * args.steps,
+            "gpu_launches": (plan.kernel_launches(True) + 1) * args.steps,
             "clocks": clk.summary(),
         }), flush=True)
 
@@ -292,6 +371,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d10")
+    ap.add_argument("--autotune", action="store_true", help="tune the exponential kernels before timing")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -233,6 +233,20 @@ int qoc_optimize_pulses(qoc_plan* plan, double* u, const double* psi0, const dou
                         double* F_hist, int* reached, int* iters_done, void* workspace, size_t workspace_bytes,
                         void* stream);
 
+/* ---------------------------------------------------------------- tuning */
+/* Kernel choice of the batched exponentials (Sec. II.A, Eq. exppropagator, as in qoc_expm_blocks):
+ * rule i applies to blocks of size m <= m_max[i] (rules are tried in increasing m_max; the first
+ * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =
+ * by size); kind 1 = warp-packed kernel (m <= 32 FP32, <= 16 FP64, not with QOC_PREC_F32), param =
+ * matrices per warp (0 = as many as fit).  Blocks no rule covers use the tiled kernel.  The plan's
+ * workspace size may change: query qoc_plan_workspace_bytes again.  An autotuner times candidate
+ * rules (paper_2309_05884_gb300/autotune.py). */
+int qoc_plan_set_expm_rules(qoc_plan* plan, int n_rules, const int* m_max, const int* kind, const int* param);
+/* The plan's current exponential launches: kind, param (R or MP), matrices per warp, largest block
+ * and block count of each; arrays of max_out entries (may be NULL). */
+int qoc_plan_expm_classes(const qoc_plan* plan, int max_out, int* n_classes, int* kind, int* param, int* per_warp,
+                          int* m_max, int* n_blocks);
+
 /* ---------------------------------------------------------------- measurement */
 /* Phase timing: when enabled, every later call records CUDA events on its stream between its
  * phases.  qoc_plan_phase_times waits for the last call and writes up to n_out durations in ms:
@@ -246,6 +260,24 @@ int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
 int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);
 /* Number of kernel launches one qoc_fidelity_and_grad (with_grad = 1) or qoc_propagate (0) call makes. */
 int qoc_plan_kernel_launches(const qoc_plan* plan, int with_grad, int* launches);
+
+/* ---------------------------------------------------------------- learned warm start */
+/* Dense layers of the warm-start network (not part of the paper: a small MLP that proposes initial
+ * pulses from a problem's parameters, trained on pulses optimised by this library's GRAPE).
+ * Row-major device arrays; W is BF16 (uint16 bits) [out][in]; activations, biases and gradients
+ * FP32; products accumulate in FP32.  act: 0 = identity, 1 = GELU(z) = z Phi(z) (exact, erf form).
+ *   forward : Z = X W^T + bias (pre-activation, kept for backward), Y = act(Z); X [B][in], Z, Y [B][out]
+ *   backward: dZ = dY * act'(Z); dX = dZ W (may be NULL); dW = dZ^T X [out][in]; db = column sums of dZ
+ * Adam (descent): m, v and param FP32 [n]; shadow (BF16, may be NULL) receives the rounded param;
+ * t counts steps from 1.  MSE: loss (dev double) = mean (Y - T)^2, dY = 2 (Y - T)/n (may be NULL). */
+int qoc_dense_forward(const float* X, const uint16_t* W, const float* bias, float* Z, float* Y, long long B, int in,
+                      int out, int act, void* stream);
+int qoc_dense_backward(const float* X, const uint16_t* W, const float* Z, const float* dY, float* dZ, float* dX,
+                       float* dW, float* db, long long B, int in, int out, int act, void* stream);
+int qoc_adam_step(float* param, uint16_t* shadow_bf16, const float* grad, float* m, float* v, long long n, float lr,
+                  float beta1, float beta2, float eps, int t, void* stream);
+int qoc_mse(const float* Y, const float* T, float* dY, double* loss, long long n, void* stream);
+int qoc_to_bf16(const float* x, uint16_t* y, long long n, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart to this entry point; it serves callers that cannot allocate device

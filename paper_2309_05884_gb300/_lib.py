@@ -83,6 +83,14 @@ SIGNATURES = {
     "qoc_plan_work_counts": (C.c_int, [P, C.POINTER(C.c_longlong), C.c_int]),
     "qoc_plan_kernel_launches": (C.c_int, [P, C.c_int, C.POINTER(C.c_int)]),
     "qoc_expm_batch_noalloc": (C.c_int, [P, P, C.c_int, C.c_longlong, P]),
+    "qoc_plan_set_expm_rules": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "qoc_plan_expm_classes": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                        C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "qoc_dense_forward": (C.c_int, [P, P, P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P]),
+    "qoc_dense_backward": (C.c_int, [P, P, P, P, P, P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P]),
+    "qoc_adam_step": (C.c_int, [P, P, P, P, P, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]),
+    "qoc_mse": (C.c_int, [P, P, P, P, C.c_longlong, P]),
+    "qoc_to_bf16": (C.c_int, [P, P, C.c_longlong, P]),
     "qoc_strerror": (C.c_char_p, [C.c_int]),
     "qoc_last_error": (C.c_char_p, []),
     "qoc_version": (C.c_int, []),

@@ -283,6 +283,28 @@ class Plan:
         L.check(self.lib.qoc_plan_work_counts(self.handle, out, 3), "qoc_plan_work_counts")
         return list(out)
 
+    def set_expm_rules(self, rules) -> None:
+        """rules: [(m_max, kind, param)], kind 0 = tiled CTA kernel (param R), 1 = warp-packed (param =
+        matrices per warp).  Reallocates the workspace if its size changes."""
+        n = len(rules)
+        mx = (C.c_int * n)(*[r[0] for r in rules])
+        kd = (C.c_int * n)(*[r[1] for r in rules])
+        pm = (C.c_int * n)(*[r[2] for r in rules])
+        L.check(self.lib.qoc_plan_set_expm_rules(self.handle, n, mx, kd, pm), "qoc_plan_set_expm_rules")
+        nbytes = C.c_size_t()
+        L.check(self.lib.qoc_plan_workspace_bytes(self.handle, C.byref(nbytes)), "qoc_plan_workspace_bytes")
+        if nbytes.value != self.workspace_bytes:
+            self.workspace_bytes = nbytes.value
+            self._ws = None
+
+    def expm_classes(self):
+        """[(kind, param, per_warp, m_max, n_blocks)] of the plan's exponential launches."""
+        n = C.c_int()
+        cap = 32
+        arrs = [(C.c_int * cap)() for _ in range(5)]
+        L.check(self.lib.qoc_plan_expm_classes(self.handle, cap, C.byref(n), *arrs), "qoc_plan_expm_classes")
+        return [tuple(a[i] for a in arrs) for i in range(n.value)]
+
     def kernel_launches(self, with_grad: bool = True) -> int:
         n = C.c_int()
         L.check(self.lib.qoc_plan_kernel_launches(self.handle, int(with_grad), C.byref(n)), "qoc_plan_kernel_launches")

@@ -26,7 +26,8 @@ constexpr int GRAD_THREADS = 512;
 template <class T> struct GradCfg;
 template <> struct GradCfg<float> { static constexpr int P = 24, CG = 2; };
 template <> struct GradCfg<double> { static constexpr int P = 40, CG = 1; };
-constexpr int MAX_SUB_LOG2 = 6;  // at most 64 sub-slices per slice
+constexpr int MAX_SUB_LOG2 = 7;  // at most 128 sub-slices per slice
+constexpr int REV_MIN_SUB = 3;   // slices needing >= 2^3 sub-slices go to reverse mode (grad_rev.cu)
 
 // ys[v] = sgn[v] * M xs[v] for v < nv (nv <= NV); M is m x m row-major (shared or global), the
 // vectors are in shared memory.  G threads share a row; M[o][j] is read once for all nv vectors.
@@ -142,6 +143,10 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
             s_sub = sub;
         }
         __syncthreads();
+        if (s_sub >= REV_MIN_SUB) {  // large-norm slice: the reverse-mode kernel (grad_rev.cu) owns it
+            __syncthreads();
+            continue;
+        }
         const int Pt = s_P;
         const int nsub = 1 << s_sub;
         const T tau_s = tau / (T)nsub;

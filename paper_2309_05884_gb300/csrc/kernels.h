@@ -29,6 +29,13 @@ int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const
 // U_out[a_off[b] + k*m*m + e] (complex128, unpadded) <- the working-precision propagators.
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st);
 
+// ---- expm_warp.cu (m <= 32: warp-packed, 32/MP matrices per warp)
+int expm_warp_mp(int prec, int m);             // MP (8, 16, 32) or 0 if the warp kernel does not apply
+int expm_warp_grid_limit(int prec, int MP);
+int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
+                     const int2* items, long long n_items, int MP, int per_warp, void* Uout, int grid,
+                     cudaStream_t st);
+
 // ---- sweep.cu
 // Forward (psi_{i+1} = U_i psi_i) and/or backward (lam_i = U_i^dagger lam_{i+1}) sweeps over the
 // current slice window of every active block, one CTA per (direction, block); dirs: 1 = forward,
@@ -52,6 +59,13 @@ size_t grad_slot_bytes(int prec, int max_m);
 // Shared memory the slice-derivative kernel needs for its vector families (without A).
 size_t grad_vector_smem(int prec, int max_m);
 int grad_grid_limit(int prec, int max_m);
+// ---- grad_rev.cu: reverse-mode slice derivatives of the slices with >= 3 squarings
+int grad_rev_min_s();
+size_t grad_rev_slot_bytes(int prec, int m_max);
+// One launch per size class (cls: the class's blocks, items: its (block, slice) pairs).
+int launch_grad_rev(const DevPlan& P, const ExpmTables& tabs, const double* u, const void* psi, const void* lam,
+                    double2* partial, char* scratch, size_t slot, int m_max, int grid, const int* cls, int n_cls,
+                    const int2* items, long long n_items, int class_m_max, cudaStream_t st);
 // Per problem p: grad[k][j] = 2 Re(conj(o_p) sum over p's blocks of the slice derivatives); then
 // the update rule on u (rule.kind < 0: none); advances rule.iter when it is set.
 int launch_grad_reduce(const DevPlan& P, const double2* partial, const double2* o_ws, double* grad, double* u,

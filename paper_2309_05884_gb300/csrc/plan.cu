@@ -17,6 +17,8 @@
 using namespace qoc;
 
 struct ExpmClass {
+    int kind;            // 0: CTA tiles (param R), 1: warp-packed (param MP, per_warp matrices per warp)
+    int per_warp;
     int R;
     int offset;          // into the class block list (windowed launches)
     int count;           // active blocks in the class
@@ -25,6 +27,13 @@ struct ExpmClass {
     int m_max;
     int grid;
     size_t slot_bytes;
+};
+
+// Kernel choice for blocks of size <= m_max (rules sorted by m_max; the first match wins).
+struct ExpmRule {
+    int m_max;
+    int kind;   // 0 CTA tiles, 1 warp-packed
+    int param;  // R (CTA) or matrices per warp (warp-packed; 0 = as many as fit)
 };
 
 struct Problem {
@@ -67,8 +76,12 @@ struct qoc_plan {
     std::vector<int> prob_blocks, prob_block_off;
     ExpmTables tabs{};
     std::vector<ExpmClass> classes;
+    std::vector<ExpmRule> rules;
+    size_t expm_scratch = 0;
     int grad_grid = 0;
     size_t grad_slot = 0;
+    int rev_grid = 0;
+    size_t rev_slot = 0;
     int seg = 0;                    // slices per checkpoint segment (single problem)
     int nseg = 1;                   // segments
     int64_t vlen = 0;               // complex elements of one boundary vector set (sum c*m)
@@ -93,9 +106,10 @@ struct qoc_plan {
     GraphKey graph_key{};
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
-           off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0;
+           off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0, off_rev = 0;
     size_t el = 16;
     size_t ws_bytes = 0;
+    int64_t u_elems = 0, s_elems = 0, part_rows = 0;
 
     DevPlan dev(int k0 = 0, int nk = -1) const {
         DevPlan P{};
@@ -165,9 +179,14 @@ char* lamb_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_lamb + (
 int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
     const DevPlan P = p->dev(k0, nk);
     for (const auto& c : p->classes) {
-        if (launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items, c.R,
-                        ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st) != 0)
-            return cuda_fail(cudaGetLastError(), "expm launch");
+        int rc;
+        if (c.kind == 1)
+            rc = launch_expm_warp(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                  c.R, c.per_warp, ws + p->off_U, c.grid, st);
+        else
+            rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items, c.R,
+                             ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st);
+        if (rc != 0) return cuda_fail(cudaGetLastError(), "expm launch");
     }
     return QOC_OK;
 }
@@ -189,6 +208,16 @@ int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
                                        p->grad_slot, p->max_m, p->grad_grid, st);
     if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
     if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
+    if (P.grad_mode == 0) {
+        // large-norm slices: reverse-mode kernel, one launch per size class with that class's tile
+        for (const auto& c : p->classes) {
+            if (launch_grad_rev(P, p->tabs, u, ws + p->off_psi, ws + p->off_lam,
+                                reinterpret_cast<double2*>(ws + p->off_partial), ws + p->off_rev, p->rev_slot, p->max_m,
+                                p->rev_grid, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                c.m_max, st) != 0)
+                return cuda_fail(cudaGetLastError(), "reverse-mode gradient launch");
+        }
+    }
     return QOC_OK;
 }
 
@@ -214,6 +243,102 @@ int forward_pass(const qoc_plan* p, const double* u, const double* psi0, char* w
             return rc;
     }
     return QOC_OK;
+}
+
+// Partition the active blocks into expm launches by the plan's rules; uploads the class lists.
+int build_classes(qoc_plan* p) {
+    const int wp = p->opts.prec;
+    struct Key { int kind, param, per_warp; };
+    std::vector<Key> keys(p->nb);
+    for (int i = 0; i < p->nb; ++i) {
+        const int m = p->hblocks[i].m;
+        Key key{0, expm_r_for(wp == QOC_PREC_F64 ? 0 : 1, m), 0};
+        for (const auto& r : p->rules) {
+            if (m > r.m_max) continue;
+            if (r.kind == 1) {
+                const int MP = expm_warp_mp(wp, m);
+                if (!MP) continue;  // not applicable: next rule
+                key = {1, MP, r.param > 0 ? std::min(r.param, 32 / MP) : 32 / MP};
+            } else {
+                const int rmax = wp == QOC_PREC_F64 ? 4 : 7;
+                key = {0, r.param > 0 ? std::min(r.param, rmax) : expm_r_for(wp == QOC_PREC_F64 ? 0 : 1, m), 0};
+            }
+            break;
+        }
+        keys[i] = key;
+    }
+    std::vector<int> cls_list;
+    std::vector<int2> cls_items;
+    p->classes.clear();
+    p->expm_scratch = 0;
+    std::vector<Key> seen;
+    for (int i = 0; i < p->nb; ++i) {
+        bool dup = false;
+        for (const auto& s : seen)
+            if (s.kind == keys[i].kind && s.param == keys[i].param && s.per_warp == keys[i].per_warp) dup = true;
+        if (!dup) seen.push_back(keys[i]);
+    }
+    for (const auto& key : seen) {
+        ExpmClass c{};
+        c.kind = key.kind;
+        c.R = key.param;
+        c.per_warp = key.per_warp;
+        c.offset = (int)cls_list.size();
+        c.item_off = (long long)cls_items.size();
+        for (int i = 0; i < p->nb; ++i)
+            if (keys[i].kind == key.kind && keys[i].param == key.param && keys[i].per_warp == key.per_warp) {
+                cls_list.push_back(i);
+                c.count++;
+                c.m_max = std::max(c.m_max, p->hblocks[i].m);
+                for (int k = 0; k < p->hblocks[i].N; ++k) cls_items.push_back(make_int2(i, k));
+            }
+        c.n_items = (long long)cls_items.size() - c.item_off;
+        const long long max_items = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
+        if (c.kind == 1) {
+            const long long groups = (max_items + c.per_warp - 1) / c.per_warp;
+            const long long ctas = (groups + (c.R == 32 ? 2 : 4) - 1) / (c.R == 32 ? 2 : 4);
+            c.grid = (int)std::max<long long>(1, std::min<long long>(ctas, expm_warp_grid_limit(wp, c.R)));
+            c.slot_bytes = 0;
+        } else {
+            c.grid = (int)std::min<long long>(max_items, expm_grid_limit(wp == QOC_PREC_F64 ? 0 : 1, c.R));
+            c.slot_bytes = align_up(expm_slot_bytes(wp == QOC_PREC_F64 ? 0 : 1, c.m_max), 256);
+            p->expm_scratch = std::max(p->expm_scratch, c.slot_bytes * (size_t)c.grid);
+        }
+        p->classes.push_back(c);
+    }
+    cudaFree(p->d_cls);
+    cudaFree(p->d_cls_items);
+    p->d_cls = nullptr;
+    p->d_cls_items = nullptr;
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_cls, sizeof(int) * std::max<size_t>(1, cls_list.size()))) != cudaSuccess)
+        return cuda_fail(e, "upload classes");
+    if ((e = cudaMalloc(&p->d_cls_items, sizeof(int2) * std::max<size_t>(1, cls_items.size()))) != cudaSuccess)
+        return cuda_fail(e, "upload classes");
+    cudaMemcpy(p->d_cls, cls_list.data(), sizeof(int) * cls_list.size(), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_cls_items, cls_items.data(), sizeof(int2) * cls_items.size(), cudaMemcpyHostToDevice);
+    return QOC_OK;
+}
+
+// Recompute the workspace layout from the plan's sizes (classes may change the expm scratch).
+void layout_workspace(qoc_plan* p, int64_t u_elems, int64_t s_elems, int64_t part_rows) {
+    const size_t el = p->el;
+    size_t off = 0;
+    p->off_U = off;       off = align_up(off + (size_t)u_elems * el, 256);
+    p->off_psi = off;     off = align_up(off + (size_t)s_elems * el, 256);
+    p->off_lam = off;     off = align_up(off + (size_t)s_elems * el, 256);
+    p->off_partial = off; off = align_up(off + (size_t)part_rows * p->nc * 16, 256);
+    p->off_o = off;       off = align_up(off + (size_t)p->n_prob * 16, 256);
+    p->off_out3 = off;    off = align_up(off + (size_t)p->n_prob * 24, 256);
+    p->off_expm = off;    off = align_up(off + p->expm_scratch, 256);
+    p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
+    p->off_rev = off;     off = align_up(off + p->rev_slot * (size_t)p->rev_grid, 256);
+    p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
+    p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
+    p->off_adam = off;    off = align_up(off + (size_t)2 * p->rows * p->nc * sizeof(double), 256);
+    p->off_iter = off;    off = align_up(off + sizeof(int), 256);
+    p->off_reached = off; off = align_up(off + (size_t)p->n_prob * sizeof(int), 256);
+    p->ws_bytes = off;
 }
 
 UpdateRule no_update() {
@@ -447,50 +572,34 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     }
     p->tabs.sq_f64 = o.prec == QOC_PREC_F32_ALL ? 0 : 1;
 
-    // expm size classes: per class, its blocks and its (block, slice) items
-    std::vector<int> cls_list;
-    std::vector<int2> cls_items;
-    size_t expm_scratch = 0;
-    for (int R = 1; R <= 7; ++R) {
-        ExpmClass c{R, (int)cls_list.size(), 0, (long long)cls_items.size(), 0, 0, 0, 0};
-        for (int i = 0; i < p->nb; ++i)
-            if (expm_r_for(wp, p->hblocks[i].m) == R) {
-                cls_list.push_back(i);
-                c.count++;
-                c.m_max = std::max(c.m_max, p->hblocks[i].m);
-                for (int k = 0; k < p->hblocks[i].N; ++k) cls_items.push_back(make_int2(i, k));
-            }
-        if (c.count == 0) continue;
-        c.n_items = (long long)cls_items.size() - c.item_off;
-        const long long max_items = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
-        c.grid = (int)std::min<long long>(max_items, expm_grid_limit(wp, R));
-        c.slot_bytes = align_up(expm_slot_bytes(wp, c.m_max), 256);
-        expm_scratch = std::max(expm_scratch, c.slot_bytes * (size_t)c.grid);
-        p->classes.push_back(c);
+    // expm size classes (default rules: warp-packed kernel for the small blocks it supports)
+    p->rules.push_back({1 << 30, 0, 0});  // tiled kernels; the autotuner may pick the warp-packed one
+    {
+        const int rc = build_classes(p);
+        if (rc) {
+            qoc_plan_free(p);
+            return rc;
+        }
     }
     // gradient kernel
     p->grad_slot = align_up(grad_slot_bytes(wp, p->max_m), 256);
     const long long grad_items = p->nseg == 1 ? (long long)p->items.size() : (long long)p->seg * p->nb;
     p->grad_grid = (int)std::min<long long>(grad_items, grad_grid_limit(wp, p->max_m));
+    // reverse-mode kernel for large-norm slices: one scratch slot per CTA, at most 256 MiB in total
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        p->rev_slot = align_up(grad_rev_slot_bytes(wp == QOC_PREC_F64 ? 0 : 1, p->max_m), 256);
+        const long long by_mem = std::max<long long>(1, (256LL << 20) / (long long)p->rev_slot);
+        p->rev_grid = (int)std::max<long long>(1, std::min<long long>({grad_items, (long long)sms, by_mem}));
+    }
 
     // workspace layout
-    const int64_t slot_total = p->nseg == 1 ? 0 : 0;
-    (void)slot_total;
-    size_t off = 0;
-    p->off_U = off;       off = align_up(off + (size_t)u_off * el, 256);
-    p->off_psi = off;     off = align_up(off + (size_t)s_off * el, 256);
-    p->off_lam = off;     off = align_up(off + (size_t)s_off * el, 256);
-    p->off_partial = off; off = align_up(off + (size_t)part_off * nc * 16, 256);
-    p->off_o = off;       off = align_up(off + (size_t)n_problems * 16, 256);
-    p->off_out3 = off;    off = align_up(off + (size_t)n_problems * 24, 256);
-    p->off_expm = off;    off = align_up(off + expm_scratch, 256);
-    p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
-    p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
-    p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
-    p->off_adam = off;    off = align_up(off + (size_t)2 * p->rows * nc * sizeof(double), 256);
-    p->off_iter = off;    off = align_up(off + sizeof(int), 256);
-    p->off_reached = off; off = align_up(off + (size_t)n_problems * sizeof(int), 256);
-    p->ws_bytes = off;
+    p->u_elems = u_off;
+    p->s_elems = s_off;
+    p->part_rows = part_off;
+    layout_workspace(p, u_off, s_off, part_off);
 
     // device uploads
     auto fail = [&](cudaError_t e, const char* what) {
@@ -510,8 +619,6 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     QOC_UP(p->d_copy_src, p->copy_src.data(), p->copy_src.size(), "upload copies");
     QOC_UP(p->d_copy_base, p->copy_base.data(), p->copy_base.size(), "upload copies");
     QOC_UP(p->d_a_off, p->a_off.data(), p->a_off.size(), "upload offsets");
-    QOC_UP(p->d_cls, cls_list.data(), cls_list.size(), "upload classes");
-    QOC_UP(p->d_cls_items, cls_items.data(), cls_items.size(), "upload class items");
     QOC_UP(p->d_items, p->items.data(), p->items.size(), "upload items");
     QOC_UP(p->d_prob_blocks, p->prob_blocks.data(), p->prob_blocks.size(), "upload problems");
     QOC_UP(p->d_prob_block_off, p->prob_block_off.data(), p->prob_block_off.size(), "upload problems");
@@ -636,10 +743,47 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     // (+ the iteration counter when optimising); propagate: gather, expm, sweep, memset, store
     const int ncls = (int)p->classes.size();
     if (p->nseg == 1)
-        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + 1 : 1 + ncls + 1 + 1;
+        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + ncls + 1 : 1 + ncls + 1 + 1;
     else
-        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (ncls + 2) + 1
+        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (2 * ncls + 2) + 1
                               : 1 + p->nseg * (ncls + 1) + 1;
+    return QOC_OK;
+}
+
+int qoc_plan_set_expm_rules(qoc_plan* p, int n_rules, const int* m_max, const int* kind, const int* param) {
+    if (!p || n_rules < 1 || !m_max || !kind || !param) return set_error(QOC_EINVAL, "null argument or no rule");
+    std::vector<ExpmRule> rules;
+    for (int i = 0; i < n_rules; ++i) {
+        if (kind[i] != 0 && kind[i] != 1) return set_error(QOC_EINVAL, "rule kind must be 0 (CTA tiles) or 1 (warp-packed)");
+        if (param[i] < 0) return set_error(QOC_EINVAL, "rule parameter must be >= 0");
+        rules.push_back({m_max[i], kind[i], param[i]});
+    }
+    std::stable_sort(rules.begin(), rules.end(), [](const ExpmRule& a, const ExpmRule& b) { return a.m_max < b.m_max; });
+    rules.push_back({1 << 30, 0, 0});  // fallback: CTA tiles sized by m
+    cudaSetDevice(p->device);
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    p->rules = rules;
+    const int rc = build_classes(p);
+    if (rc) return rc;
+    layout_workspace(p, p->u_elems, p->s_elems, p->part_rows);
+    return QOC_OK;
+}
+
+int qoc_plan_expm_classes(const qoc_plan* p, int max_out, int* n_classes, int* kind, int* param, int* per_warp,
+                          int* m_max, int* n_blocks) {
+    if (!p || !n_classes) return set_error(QOC_EINVAL, "null argument");
+    *n_classes = (int)p->classes.size();
+    for (int i = 0; i < (int)p->classes.size() && i < max_out; ++i) {
+        const auto& c = p->classes[i];
+        if (kind) kind[i] = c.kind;
+        if (param) param[i] = c.R;
+        if (per_warp) per_warp[i] = c.per_warp;
+        if (m_max) m_max[i] = c.m_max;
+        if (n_blocks) n_blocks[i] = c.count;
+    }
     return QOC_OK;
 }
 

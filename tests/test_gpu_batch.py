@@ -111,3 +111,51 @@ def test_batched_adam_graph_replay_matches_oracle():
         n_hist = len(hist)
         assert np.abs(Fg.cpu().numpy()[:n_hist, i] - np.array(hist)).max() <= 1e-9
         row += p.N
+
+
+def test_warp_packed_and_tiled_kernels_agree():
+    probs = I.sn_problem_batch(6, base_seed=23_000, n_lo=3, n_hi=15, N_lo=10, N_hi=30)
+    plan, systems, d0, df, us = make_batch(probs, 1.0, "f64")
+    u = np.concatenate(us)
+    plan.set_expm_rules([(16, 1, 0)])                         # warp-packed kernel for the small blocks
+    assert any(c[0] == 1 for c in plan.expm_classes())
+    out_w, g_w = run(plan, u, d0, df)
+    plan.set_expm_rules([(64, 0, 0)])                         # force the tiled kernel
+    assert all(c[0] == 0 for c in plan.expm_classes())
+    out_t, g_t = run(plan, u, d0, df)
+    assert np.abs(out_w - out_t).max() <= 1e-12
+    assert np.abs(g_w - g_t).max() <= 1e-12 * max(1.0, np.abs(g_t).max())
+    plan.set_expm_rules([(16, 1, 1)])                         # one matrix per warp
+    out_1, g_1 = run(plan, u, d0, df)
+    # packing changes which matrices share a warp-uniform scaling, so agreement is to rounding
+    assert np.abs(out_1 - out_w).max() <= 1e-12
+    assert np.abs(g_1 - g_w).max() <= 1e-12 * max(1.0, np.abs(g_w).max())
+
+
+def test_autotuner_keeps_results(tmp_path):
+    from paper_2309_05884_gb300 import autotune
+    probs = I.sn_problem_batch(8, base_seed=24_000, n_lo=6, n_hi=40, N_lo=20, N_hi=40)
+    plan, systems, d0, df, us = make_batch(probs, 1.0, "f32_all")
+    ut = torch.from_numpy(np.concatenate(us)).to(DEV)
+    out0, g0 = run(plan, ut.cpu().numpy(), d0, df)
+    rep = autotune.tune_expm(plan, ut, d0, df, reps=2, cache_path=str(tmp_path / "tune.json"))
+    assert rep["rules"] and rep["tuned_ms"] > 0 and len(rep["trials"]) >= 2
+    out1, g1 = run(plan, ut.cpu().numpy(), d0, df)
+    assert np.abs(out1 - out0).max() <= 1e-5
+    rep2 = autotune.tune_expm(plan, ut, d0, df, cache_path=str(tmp_path / "tune.json"))
+    assert rep2["cached"] and [tuple(r) for r in rep2["rules"]] == [tuple(r) for r in rep["rules"]]
+
+
+@pytest.mark.parametrize("prec", ["f32_all", "f32"])
+def test_t10_twisting_regime_fp32(prec):
+    # T = 10 (many squarings and sub-stepped derivatives: |tau H| up to ~50)
+    probs = I.sn_problem_batch(4, base_seed=25_000, n_lo=8, n_hi=24, N_lo=200, N_hi=300)
+    T = 10.0
+    plan, systems, d0, df, us = make_batch(probs, T, prec)
+    out, g = run(plan, np.concatenate(us), d0, df)
+    row = 0
+    for i, p in enumerate(probs):
+        F, o, gref = gr.fidelity_and_grad(oracle_block(p.n, p.J, p.h, p.k_target), us[i], T / p.N)
+        assert abs(out[i, 0] - F) <= 1e-5, (prec, i, out[i, 0], F)
+        assert np.linalg.norm(g[row: row + p.N] - gref) / np.linalg.norm(gref) <= 1e-4, (prec, i)
+        row += p.N

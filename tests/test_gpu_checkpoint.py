@@ -58,7 +58,8 @@ def test_checkpointed_equals_stored_fp32_c2_full_size():
     u = I.pulses_normal(1, s.N, 3)
     _, p0, d0, df = make(s, psi0, psif, "f32", 0)
     _, p1, _, _ = make(s, psi0, psif, "f32", -1)   # S = 23, 22 segments, last one ragged (17 slices)
-    assert p1.workspace_bytes * 3 < p0.workspace_bytes
+    # the stored propagators (500 slices x 53 764 complex64 = 215 MB) shrink to one segment's worth
+    assert p0.workspace_bytes - p1.workspace_bytes > 0.9 * 500 * 53764 * 8
     o0, g0 = eval_(p0, u, d0, df)
     o1, g1 = eval_(p1, u, d0, df)
     assert np.array_equal(o0, o1) and np.array_equal(g0, g1)
