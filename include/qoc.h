@@ -238,7 +238,8 @@ int qoc_optimize_pulses(qoc_plan* plan, double* u, const double* psi0, const dou
  * rule i applies to blocks of size m <= m_max[i] (rules are tried in increasing m_max; the first
  * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =
  * by size); kind 1 = warp-packed kernel (m <= 32 FP32, <= 16 FP64, not with QOC_PREC_F32), param =
- * matrices per warp (0 = as many as fit).  Blocks no rule covers use the tiled kernel.  The plan's
+ * matrices per warp (0 = as many as fit); kind 2 = tcgen05 tensor-core kernel (FP32 plans, m <= 112;
+ * products as in qoc_tc_cgemm).  Blocks no rule covers use the tiled kernel.  The plan's
  * workspace size may change: query qoc_plan_workspace_bytes again.  An autotuner times candidate
  * rules (paper_2309_05884_gb300/autotune.py). */
 int qoc_plan_set_expm_rules(qoc_plan* plan, int n_rules, const int* m_max, const int* kind, const int* param);
@@ -260,6 +261,15 @@ int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
 int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);
 /* Number of kernel launches one qoc_fidelity_and_grad (with_grad = 1) or qoc_propagate (0) call makes. */
 int qoc_plan_kernel_launches(const qoc_plan* plan, int with_grad, int* launches);
+
+/* ---------------------------------------------------------------- tensor-core products */
+/* Batched complex products C[i] = A[i] B[i] on the 5th-generation tensor cores (tcgen05, kind::f16)
+ * at about FP32 accuracy: every real part is split into two FP16 numbers (hi + lo) and the products
+ * keep hi*hi + hi*lo + lo*hi with FP32 accumulation.  This is the building block of the matrix
+ * exponentials of Eq. exppropagator (Sec. II.A) on the tensor cores.  A, B, C: dev, count complex64
+ * (interleaved float) m x m row-major matrices each; m <= 112.  status (dev int, may be NULL): a
+ * bounded wait that gave up sets bit 8.  Asynchronous on stream. */
+int qoc_tc_cgemm(const float* A, const float* B, float* C, int m, long long count, int* status, void* stream);
 
 /* ---------------------------------------------------------------- learned warm start */
 /* Dense layers of the warm-start network (not part of the paper: a small MLP that proposes initial

@@ -91,6 +91,7 @@ SIGNATURES = {
     "qoc_adam_step": (C.c_int, [P, P, P, P, P, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, P]),
     "qoc_mse": (C.c_int, [P, P, P, P, C.c_longlong, P]),
     "qoc_to_bf16": (C.c_int, [P, P, C.c_longlong, P]),
+    "qoc_tc_cgemm": (C.c_int, [P, P, P, C.c_int, C.c_longlong, P, P]),
     "qoc_strerror": (C.c_char_p, [C.c_int]),
     "qoc_last_error": (C.c_char_p, []),
     "qoc_version": (C.c_int, []),

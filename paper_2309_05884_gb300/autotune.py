@@ -36,6 +36,8 @@ def _candidates(m_max: int, prec: str) -> List[Tuple[int, int]]:
     rmax = 4 if prec == "f64" else 7
     r0 = max(1, min(rmax, -(-m_max // 16)))
     out = [(0, r) for r in sorted({max(1, r0 - 1), r0, min(rmax, r0 + 1)})]
+    if prec != "f64" and m_max <= 112:
+        out.append((2, 0))  # tcgen05 tensor cores
     warp_ok = prec != "f32" and m_max <= (16 if prec == "f64" else 32)
     if warp_ok:
         mp = 8 if m_max <= 8 else 16 if m_max <= 16 else 32

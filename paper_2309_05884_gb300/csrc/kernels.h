@@ -36,6 +36,13 @@ int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, 
                      const int2* items, long long n_items, int MP, int per_warp, void* Uout, int grid,
                      cudaStream_t st);
 
+// ---- expm_tc.cu (tcgen05 tensor cores, FP16-split products; FP32 plans, m <= 112)
+int expm_tc_supported(int prec, int m);
+int expm_tc_grid_limit();
+int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
+                   const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
+                   int grid, cudaStream_t st);
+
 // ---- sweep.cu
 // Forward (psi_{i+1} = U_i psi_i) and/or backward (lam_i = U_i^dagger lam_{i+1}) sweeps over the
 // current slice window of every active block, one CTA per (direction, block); dirs: 1 = forward,

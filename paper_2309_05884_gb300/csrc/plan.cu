@@ -183,6 +183,9 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
         if (c.kind == 1)
             rc = launch_expm_warp(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                   c.R, c.per_warp, ws + p->off_U, c.grid, st);
+        else if (c.kind == 2)
+            rc = launch_expm_tc(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st);
         else
             rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items, c.R,
                              ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st);
@@ -259,6 +262,9 @@ int build_classes(qoc_plan* p) {
                 const int MP = expm_warp_mp(wp, m);
                 if (!MP) continue;  // not applicable: next rule
                 key = {1, MP, r.param > 0 ? std::min(r.param, 32 / MP) : 32 / MP};
+            } else if (r.kind == 2) {
+                if (!expm_tc_supported(wp, m)) continue;
+                key = {2, 0, 0};
             } else {
                 const int rmax = wp == QOC_PREC_F64 ? 4 : 7;
                 key = {0, r.param > 0 ? std::min(r.param, rmax) : expm_r_for(wp == QOC_PREC_F64 ? 0 : 1, m), 0};
@@ -294,7 +300,11 @@ int build_classes(qoc_plan* p) {
             }
         c.n_items = (long long)cls_items.size() - c.item_off;
         const long long max_items = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
-        if (c.kind == 1) {
+        if (c.kind == 2) {
+            c.grid = (int)std::max<long long>(1, std::min<long long>(max_items, expm_tc_grid_limit()));
+            c.slot_bytes = align_up(expm_slot_bytes(1, c.m_max), 256);
+            p->expm_scratch = std::max(p->expm_scratch, c.slot_bytes * (size_t)c.grid);
+        } else if (c.kind == 1) {
             const long long groups = (max_items + c.per_warp - 1) / c.per_warp;
             const long long ctas = (groups + (c.R == 32 ? 2 : 4) - 1) / (c.R == 32 ? 2 : 4);
             c.grid = (int)std::max<long long>(1, std::min<long long>(ctas, expm_warp_grid_limit(wp, c.R)));
@@ -754,7 +764,8 @@ int qoc_plan_set_expm_rules(qoc_plan* p, int n_rules, const int* m_max, const in
     if (!p || n_rules < 1 || !m_max || !kind || !param) return set_error(QOC_EINVAL, "null argument or no rule");
     std::vector<ExpmRule> rules;
     for (int i = 0; i < n_rules; ++i) {
-        if (kind[i] != 0 && kind[i] != 1) return set_error(QOC_EINVAL, "rule kind must be 0 (CTA tiles) or 1 (warp-packed)");
+        if (kind[i] < 0 || kind[i] > 2)
+            return set_error(QOC_EINVAL, "rule kind must be 0 (CTA tiles), 1 (warp-packed) or 2 (tensor cores)");
         if (param[i] < 0) return set_error(QOC_EINVAL, "rule parameter must be >= 0");
         rules.push_back({m_max[i], kind[i], param[i]});
     }
