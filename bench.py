@@ -284,6 +284,10 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]()
     plan, u0, b0, bf = wl.build(api, dev)
+    if args.expm_kernel == "tc":
+        plan.set_expm_rules([(112, 2, 0)])      # tcgen05 tensor cores where the block fits
+    elif args.expm_kernel == "tiled":
+        plan.set_expm_rules([(1 << 30, 0, 0)])
     if args.autotune:
         from paper_2309_05884_gb300 import autotune
         autotune.tune_expm(plan, torch.from_numpy(u0).to(dev), api.to_device(b0, dev), api.to_device(bf, dev),
@@ -410,6 +414,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d10")
     ap.add_argument("--autotune", action="store_true", help="tune the exponential kernels before timing")
+    ap.add_argument("--expm-kernel", choices=["default", "tiled", "tc"], default="default",
+                    help="force the exponential kernel: tiled CUDA-core or tcgen05 tensor-core")
     ap.add_argument("--ws-train", type=int, default=WS_TRAIN, help="warm-start training problems")
     ap.add_argument("--ws-held", type=int, default=WS_HELD, help="warm-start held-out problems")
     args = ap.parse_args()
