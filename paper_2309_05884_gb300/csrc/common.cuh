@@ -43,6 +43,7 @@ enum : int {
     ST_SQUARING_CAP = 2,    // a slice needed more squarings than the cap
     ST_SERIES_CAP = 4,      // a slice's gradient series did not reach its tolerance
     ST_TIMEOUT = 8,         // a bounded wait on an asynchronous copy gave up
+    ST_RANGE = 16,          // a tensor-core operand left the range of its FP16 split
 };
 
 // Per-active-block table, in device memory (one entry per active block of every problem).

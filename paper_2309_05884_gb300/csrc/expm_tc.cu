@@ -1,105 +1,210 @@
 // Batched slice propagators on the tcgen05 tensor cores (Sec. II.A, Eq. exppropagator).
 //
-// The method is that of expm.cu — Taylor polynomial of degree p*q by Paterson-Stockmeyer on
-// X = A/2^s, then s squarings — but every complex product runs on the tensor cores through the
-// FP16-split scheme of tc_gemm.cuh (about FP32 accuracy).  One CTA of 128 threads owns one
-// (slice, block) item at a time; X, its powers and the Horner iterates live in FP32 in the CTA's
-// global scratch slot (they feed the Horner sums), the operands of each product are staged into
-// shared memory from there.  The right-hand factor is staged once per run of products that share it
-// (X for the powers, X^p for the Horner steps).  Squarings run on the tensor cores when the plan
-// keeps them in FP32; plans with an FP64 squaring chain square in FP64 on the CUDA cores.
+// U = exp(X)^(2^s), X = -i (tau / 2^s) H_k, for blocks of size m <= 112 in FP32 plans.  Every complex
+// product runs on the tensor cores through the FP16 hi/lo split of tc_gemm.cuh (three real products
+// per real product, FP32 accumulation in tensor memory), and the operands stay on chip from one
+// product to the next: the epilogue that drains an accumulator writes the next product's operands,
+// already split, straight into shared memory.
+//
+// Polynomial.  The Taylor polynomial of odd degree 2q-1 is evaluated by Horner's rule in Y = X^2,
+//     T(X) = sum_{j<q} (c_{2j} I + c_{2j+1} X) Y^j,   c_k = 1/k!,
+// so each step S <- S Y + c_{2j+1} X + c_{2j} I needs only X beside the accumulator, and X stays in
+// tensor memory for the whole item: q products for degree 2q-1 (Y, then q-1 Horner steps).  Per
+// slice, the norm bound beta = tau (|H0|_1 + sum_j |u_j| |Hc_j|_1) fixes the fewest squarings s that
+// bring it under the plan's largest norm, then the lowest odd degree whose truncation bound covers
+// beta / 2^s.  With an FP64 squaring chain the squarings run on the CUDA cores.
+//
+// Layouts.  A product D = A B takes A as an M x K operand (rows of A, K-major) and B as its transpose
+// B^T (rows of B^T, K-major), both in 8 x 16-byte core matrices without swizzle.  A transposed copy of
+// a result comes from the same product with the operands swapped, (AB)^T = B^T A^T, so every
+// epilogue writes rows: Y^T for the Horner steps, (S^2)^T beside S^2 in the squarings, and S^T (from
+// a product with the identity) before the first squaring.
+//
+// Shared memory: four B^T planes (re hi, re lo, im hi, im lo; NP x NP halves each, NP = m rounded up
+// to 16), four A planes, then slack: an MMA with M = 128 reads 128 rows of its A operand, so the rows
+// past NP of the last plane read into the slack; the matching accumulator rows are never used.
+// Tensor memory: two accumulators of 2 x cs columns (re, im; cs = NP rounded up to a power of two,
+// at least 32): R0 at column 0 and R1 at column 2 cs.  R1 holds X during the polynomial.
+//
+// Scaling.  Each operand is scaled by a power of two 2^e before the split so that its entries stay
+// within 2^14 (the FP16 range is 65504): X by its norm bound beta, Y by beta^2, the Horner iterates by
+// e^beta, the squaring iterates by 2 (they are unitary up to rounding for Hermitian H).  An entry
+// outside the range latches ST_RANGE.  Two FP16 halves hold 22 significant bits, so a product's
+// rounding is about 2^-22 relative (FP32: 2^-24).
+#include <cuda_fp16.h>
+
 #include "../../include/qoc.h"
 #include "kernels.h"
-#include "tc_gemm.cuh"
+#include "tcgen05.cuh"
 
 namespace qoc {
 namespace {
 
-__constant__ int t_deg_p[9] = {2, 2, 3, 3, 4, 4, 5, 5, 5};
-__constant__ int t_deg_q[9] = {1, 2, 2, 3, 3, 4, 4, 5, 6};
-constexpr uint64_t TC_WAIT_NS = 2000000000ull;
+constexpr int XT_THREADS = 256;  // 8 warps: warp w drains TMEM lanes 32 (w % 4).., column groups w / 4 + 2 t
+constexpr int XT_MAXM = 112;
+constexpr uint64_t XT_WAIT_NS = 2000000000ull;
 
-// C = (staged A)(staged B) into tmem; then out[e] = acc + sum_{l<nterm} coef_l P_l (P_0 = I) for
-// the m x m entries.  Returns false if the commit did not arrive in time.
-__device__ bool tc_product_out(unsigned char* sm, const TcLayout& L, uint32_t tmem, uint64_t* bar, uint32_t& phase,
-                               float2* out, int m, int nterm, const float* coef, const float2* const* pw) {
-    fence_proxy_async_smem();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        tc_fence_after();
-        tc_issue(sm, L, tmem, bar);
-    }
-    const bool ok = mbar_wait_bounded(bar, phase, TC_WAIT_NS);
-    if (__syncthreads_or(!ok)) return false;
-    phase ^= 1u;
-    tc_fence_after();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int row = 32 * warp + lane;
-    const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-    for (int c0 = 0; c0 < L.NP; c0 += 16) {
-        float vr[16], vi[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)c0, vr);
-        tmem_ld16(tmem + lane_base + 128u + (uint32_t)c0, vi);
-        if (row < m) {
+__host__ __device__ inline int xt_pad16(int m) { return (m + 15) / 16 * 16; }
+__host__ __device__ inline int xt_cs(int NP) {
+    int c = 32;
+    while (c < NP) c <<= 1;
+    return c;
+}
+// dynamic shared memory of one CTA for operand size NP: 8 planes + the overread slack
+__host__ __device__ inline size_t xt_smem(int NP) { return ((size_t)8 * NP * NP + (size_t)(128 - NP) * NP) * 2; }
+
+// Split 8 values (scaled by sig) into FP16 hi and lo parts, packed two per word in column order.
+__device__ __forceinline__ void split8(const float (&v)[8], float sig, uint4& hi, uint4& lo, bool& bad) {
+    uint32_t h[4], l[4];
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-                const int col = c0 + j;
-                if (col >= m) continue;
-                const size_t o = (size_t)row * m + col;
-                float2 v = make_float2(vr[j], vi[j]);
-                if (nterm > 0 && row == col) v.x += coef[0];
-                for (int l = 1; l < nterm; ++l) {
-                    const float2 x = pw[l][o];
-                    v.x = fmaf(coef[l], x.x, v.x);
-                    v.y = fmaf(coef[l], x.y, v.y);
-                }
-                out[o] = v;
-            }
+    for (int i = 0; i < 4; ++i) {
+        const float a = v[2 * i] * sig, b = v[2 * i + 1] * sig;
+        bad |= !(fabsf(a) <= 65504.f) || !(fabsf(b) <= 65504.f);
+        const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
+        const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
+        const __half2 hh = __halves2half2(ah, bh), ll = __halves2half2(al, bl);
+        h[i] = *reinterpret_cast<const uint32_t*>(&hh);
+        l[i] = *reinterpret_cast<const uint32_t*>(&ll);
+    }
+    hi = make_uint4(h[0], h[1], h[2], h[3]);
+    lo = make_uint4(l[0], l[1], l[2], l[3]);
+}
+
+// Write row r, columns 8g..8g+7 of a complex matrix into the four planes starting at byte offset grp.
+__device__ __forceinline__ void put8(unsigned char* sm, uint32_t grp, uint32_t plane, int NP, int r, int g,
+                                     const float (&re)[8], const float (&im)[8], float sig, bool& bad) {
+    const uint32_t off = (uint32_t)((((r >> 3) * (NP >> 3) + g) << 6) + ((r & 7) << 3)) * 2u;
+    uint4 hi, lo;
+    split8(re, sig, hi, lo, bad);
+    *reinterpret_cast<uint4*>(sm + grp + off) = hi;
+    *reinterpret_cast<uint4*>(sm + grp + plane + off) = lo;
+    split8(im, sig, hi, lo, bad);
+    *reinterpret_cast<uint4*>(sm + grp + 2 * plane + off) = hi;
+    *reinterpret_cast<uint4*>(sm + grp + 3 * plane + off) = lo;
+}
+
+// Read columns col..col+7 of the re and im planes of an accumulator (one TMEM lane per thread).
+__device__ __forceinline__ void ld_acc8(uint32_t t_re, uint32_t t_im, float (&re)[8], float (&im)[8]) {
+    uint32_t a[8], b[8];
+    tmem_ld8_nowait(t_re, a);
+    tmem_ld8_nowait(t_im, b);
+    tmem_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        re[i] = __uint_as_float(a[i]);
+        im[i] = __uint_as_float(b[i]);
+    }
+}
+
+// One thread: D(re at d_re, im at d_im) = A B for the complex operands whose plane groups start at
+// shared addresses a and b (A as rows, B as rows of B^T), three split products per real product.
+__device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t plane, int NP, uint32_t d_re,
+                                            uint32_t d_im) {
+    const uint32_t lbo = 128, sbo = (uint32_t)(NP >> 3) * 128u;
+    const uint32_t pos = idesc_f16(128, NP, false), neg = idesc_f16(128, NP, true);
+    const int ha[3] = {0, 0, 1}, hb[3] = {0, 1, 0};  // (hi,hi), (hi,lo), (lo,hi)
+    for (int kk = 0; kk < NP / 16; ++kk) {
+        const uint32_t step = (uint32_t)kk * 256u;
+#pragma unroll
+        for (int t = 0; t < 3; ++t) {
+            const int acc = (kk > 0 || t > 0);
+            const uint64_t ar = smem_desc_u32(a + ha[t] * plane + step, lbo, sbo);
+            const uint64_t ai = smem_desc_u32(a + (2 + ha[t]) * plane + step, lbo, sbo);
+            const uint64_t br = smem_desc_u32(b + hb[t] * plane + step, lbo, sbo);
+            const uint64_t bi = smem_desc_u32(b + (2 + hb[t]) * plane + step, lbo, sbo);
+            mma_f16(d_re, ar, br, pos, acc);
+            mma_f16(d_re, ai, bi, neg, 1);
+            mma_f16(d_im, ar, bi, pos, acc);
+            mma_f16(d_im, ai, br, pos, 1);
+        }
+    }
+}
+
+// One thread: D = I_part B, with the identity (hi plane only) at shared address id and B's planes at
+// b: D = B^T, exactly the split sum hi + lo of each entry.
+__device__ __forceinline__ void issue_ident(uint32_t id, uint32_t b, uint32_t plane, int NP, uint32_t d_re,
+                                            uint32_t d_im) {
+    const uint32_t lbo = 128, sbo = (uint32_t)(NP >> 3) * 128u;
+    const uint32_t pos = idesc_f16(128, NP, false);
+    for (int kk = 0; kk < NP / 16; ++kk) {
+        const uint32_t step = (uint32_t)kk * 256u;
+        const uint64_t ai = smem_desc_u32(id + step, lbo, sbo);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int acc = (kk > 0 || h > 0);
+            mma_f16(d_re, ai, smem_desc_u32(b + h * plane + step, lbo, sbo), pos, acc);
+            mma_f16(d_im, ai, smem_desc_u32(b + (2 + h) * plane + step, lbo, sbo), pos, acc);
+        }
+    }
+}
+
+// power-of-two scale exponent for entries bounded by 'bound'
+__device__ __forceinline__ int xt_exp_for(double bound) {
+    if (!(bound > 0.0)) return 40;
+    const int e = 14 - (int)ceil(log2(bound));
+    return e < -30 ? -30 : (e > 40 ? 40 : e);
+}
+
+// Make this thread's shared-memory operand writes visible to the tensor cores and its TMEM reads
+// complete, then meet the other threads.
+__device__ __forceinline__ void xt_sync() {
+    fence_proxy_async_smem();
+    tc_fence_before();
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(XT_THREADS, 1)
+expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int* __restrict__ cls_blocks, int n_cls,
+               const int2* __restrict__ cls_items, long long n_cls_items, void* __restrict__ Uout,
+               char* __restrict__ scratch, size_t slot_bytes, int m_max, uint32_t tmem_cols) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ uint64_t bar;
+    __shared__ uint32_t tslot;
+    __shared__ float s_uf[8];
+    __shared__ float s_c[36];  // 1/k!
+    __shared__ int s_q, s_s, s_eX, s_eY, s_eS;
+    __shared__ float s_sc;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int quarter = warp & 3, half = warp >> 2;
+    const int r = 32 * quarter + lane;  // accumulator row (TMEM lane) this thread drains
+    const uint32_t lane_bits = (uint32_t)(32 * quarter) << 16;
+    if (warp == 0) {
+        tmem_alloc(&tslot, tmem_cols);
+        tmem_relinquish();
+    }
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        double f = 1.0;
+        for (int i = 0; i < 36; ++i) {
+            s_c[i] = (float)f;
+            f /= (double)(i + 1);
         }
     }
     tc_fence_before();
     __syncthreads();
-    return true;
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 1)
-expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int* __restrict__ cls_blocks, int n_cls,
-               const int2* __restrict__ cls_items, long long n_cls_items, void* __restrict__ Uout,
-               char* __restrict__ scratch, size_t slot_bytes, int m_max, TcLayout L) {
-    extern __shared__ __align__(1024) unsigned char sm[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + L.bar_off());
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + L.bar_off() + 8);
-    __shared__ float coef[8];
-    __shared__ const float2* pw[8];
-    __shared__ double s_if[32];
-    __shared__ double s_uk[8];
-    __shared__ double s_scale;
-    __shared__ int s_sq, s_p, s_q;
-    const int warp = threadIdx.x >> 5;
-    if (warp == 0) {
-        tmem_alloc(tslot, TC_TMEM_COLS);
-        tmem_relinquish();
-    }
-    if (threadIdx.x == 0) {
-        mbar_init(bar, 1);
-        fence_mbar_init();
-        double f = 1.0;
-        for (int i = 0; i < 32; ++i) { s_if[i] = f; f /= (double)(i + 1); }
-    }
-    tc_fence_before();
-    __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tslot;
+    const uint32_t tmem = tslot;
+    const uint32_t cs = tmem_cols / 4;
+    const uint32_t T0re = tmem, T0im = tmem + cs, T1re = tmem + 2 * cs, T1im = tmem + 3 * cs;  // MMA targets
+    const uint32_t R0re = T0re + lane_bits, R0im = T0im + lane_bits;  // this warp's lanes
+    const uint32_t R1re = T1re + lane_bits, R1im = T1im + lane_bits;
+    const uint32_t sm_base = smem_u32(sm);
     uint32_t phase = 0;
-    bool failed = false;
+    bool failed = false, bad = false;
 
     const size_t mm_max = (size_t)m_max * m_max;
-    float2* base = reinterpret_cast<float2*>(scratch + (size_t)blockIdx.x * slot_bytes);
-    float2* S0 = base + 6 * mm_max;
-    float2* S1 = base + 7 * mm_max;
-    double2* D0 = reinterpret_cast<double2*>(base + 8 * mm_max);
+    double2* D0 = reinterpret_cast<double2*>(scratch + (size_t)blockIdx.x * slot_bytes);
     double2* D1 = D0 + mm_max;
-    if (threadIdx.x < 8) pw[threadIdx.x] = base + (size_t)(threadIdx.x < 6 ? threadIdx.x : 0) * mm_max;
+
+    // wait for the commit of the MMAs just issued; false if it did not arrive in time
+    auto mma_wait = [&]() -> bool {
+        const bool ok = mbar_wait_bounded(&bar, phase, XT_WAIT_NS);
+        if (__syncthreads_or(!ok)) return false;
+        phase ^= 1u;
+        tc_fence_after();
+        return true;
+    };
 
     const bool whole = P.nk < 0;
     const long long total = whole ? n_cls_items : (long long)n_cls * P.nk;
@@ -116,104 +221,264 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             k = P.k0 + kw;
         }
         const DevBlock& B = P.blocks[bi];
-        const int m = B.m;
+        const int m = B.m, NP = xt_pad16(m), nkg = NP / 8;
         const size_t mm = (size_t)m * m;
+        const uint32_t plane = (uint32_t)NP * NP * 2u;
+        const uint32_t oBT = 0, oA = 4 * plane;  // plane groups (byte offsets)
+        const uint32_t aBT = sm_base + oBT, aA = sm_base + oA;
         if (threadIdx.x == 0) {
             double beta = B.h0_norm1;
-            int bad = 0;
+            int nan = 0;
             for (int j = 0; j < P.nc; ++j) {
                 const double x = u[(size_t)(B.u_row + k) * P.nc + j];
                 const int fin = isfinite(x);
-                bad |= !fin;
-                s_uk[j] = fin ? x : 0.0;
-                beta += fabs(s_uk[j]) * B.hc_norm1[j];
+                nan |= !fin;
+                s_uf[j] = fin ? (float)x : 0.f;
+                beta += fabs(fin ? x : 0.0) * B.hc_norm1[j];
             }
-            if (bad) atomicOr(P.status, ST_NAN_PULSE);
+            if (nan) atomicOr(P.status, ST_NAN_PULSE);
             beta *= B.dt;
-            int s = 0;
-            while (beta > tabs.theta_cap && s < P.max_sq) { beta *= 0.5; ++s; }
-            if (beta > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
-            int di = 0;
-            while (di < tabs.n_deg - 1 && tabs.theta[di] < beta) ++di;
-            s_sq = s;
-            s_p = t_deg_p[di];
-            s_q = t_deg_q[di];
-            s_scale = B.dt / (double)(1LL << s);
+            // Fewest squarings: each one doubles the error of what it squares, and a squaring here
+            // rounds at about 2^-22 (the split), so scaling further than the plan's largest
+            // norm loses more than the lower-degree polynomial gains.
+            const double cap = tabs.theta_cap;
+            int smin = 0;
+            double b = beta;
+            while (b > cap && smin < P.max_sq) { b *= 0.5; ++smin; }
+            if (b > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
+            // fewest squarings (each one doubles the rounding error of the polynomial), then the
+            // lowest odd degree whose truncation bound covers the scaled norm
+            const int bs = smin;
+            int bq = 1;
+            while (bq < 16 && tabs.theta_odd[bq - 1] < ldexp(beta, -bs)) ++bq;
+            const double bsn = ldexp(beta, -bs);
+            s_q = bq;
+            s_s = bs;
+            s_sc = (float)ldexp(B.dt, -bs);
+            s_eX = xt_exp_for(bsn);
+            s_eY = xt_exp_for(bsn * bsn);
+            s_eS = xt_exp_for(exp(bsn));
             if (P.stats) {
                 const unsigned long long m3 = (unsigned long long)m * m * m;
-                atomicAdd(P.stats + 0, m3 * (unsigned long long)(s_p + s_q - 2));
-                atomicAdd(P.stats + 1, m3 * (unsigned long long)s);
+                atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
+                atomicAdd(P.stats + 1, m3 * (unsigned long long)bs);
                 atomicAdd(P.stats + 2, 1ull);
             }
         }
         __syncthreads();
-        const int s = s_sq, p = s_p, q = s_q, d = p * q;
-        // X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j)
+        const int q = s_q, s = s_s;
+        const int eX = s_eX, eY = s_eY, eS = s_eS, eQ = 13;
+        const bool sq64 = s > 0 && tabs.sq_f64;
+        float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
+
+        // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1, columns into B^T
         {
             const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
-            const float sc = (float)s_scale;
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                float2 h = H[e];
-                for (int j = 0; j < P.nc; ++j) {
-                    const float2 hc = H[(size_t)(1 + j) * mm + e];
-                    const float uj = (float)s_uk[j];
-                    h.x = fmaf(uj, hc.x, h.x);
-                    h.y = fmaf(uj, hc.y, h.y);
+            const float sc = s_sc, sig = ldexpf(1.f, eX);
+            for (int g = half; g < nkg; g += 2) {
+                float xr[8], xi[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int col = 8 * g + c;
+                    float2 h = make_float2(0.f, 0.f);
+                    if (r < m && col < m) {
+                        const size_t e = (size_t)r * m + col;
+                        h = H[e];
+                        for (int j = 0; j < P.nc; ++j) {
+                            const float2 hc = H[(size_t)(1 + j) * mm + e];
+                            h.x = fmaf(s_uf[j], hc.x, h.x);
+                            h.y = fmaf(s_uf[j], hc.y, h.y);
+                        }
+                    }
+                    xr[c] = h.y * sc;
+                    xi[c] = -h.x * sc;
                 }
-                base[mm_max + e] = make_float2(h.y * sc, -h.x * sc);
+                if (r < NP) put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
+                tmem_st8(R1re + 8 * g, xr);
+                tmem_st8(R1im + 8 * g, xi);
             }
-        }
-        __syncthreads();
-        // powers X^2..X^p: B = X staged once
-        if (p >= 2) tc_stage_b(sm, L, base + mm_max, m);
-        for (int l = 2; l <= p && !failed; ++l) {
-            tc_stage_a(sm, L, base + (size_t)(l - 1) * mm_max, m);
-            if (!tc_product_out(sm, L, tmem, bar, phase, base + (size_t)l * mm_max, m, 0, nullptr, nullptr))
-                failed = true;
-        }
-        if (failed) break;
-        // S = c_d X^p + sum_{l<p} c_{(q-1)p+l} X^l
-        float2* S = S0;
-        float2* Sn = S1;
-        {
-            const int b0 = (q - 1) * p;
-            const float2* Xpp = base + (size_t)p * mm_max;
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                const int row = (int)(e / m), col = (int)(e - (size_t)row * m);
-                float2 v = make_float2(Xpp[e].x * (float)s_if[d], Xpp[e].y * (float)s_if[d]);
-                if (row == col) v.x += (float)s_if[b0];
-                for (int l = 1; l < p; ++l) {
-                    const float2 x = pw[l][e];
-                    const float c = (float)s_if[b0 + l];
-                    v.x = fmaf(c, x.x, v.x);
-                    v.y = fmaf(c, x.y, v.y);
+            for (int g = half; g < nkg; g += 2) {
+                float xr[8], xi[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const int row = 8 * g + c;  // column r of X is row r of X^T
+                    float2 h = make_float2(0.f, 0.f);
+                    if (r < m && row < m) {
+                        const size_t e = (size_t)row * m + r;
+                        h = H[e];
+                        for (int j = 0; j < P.nc; ++j) {
+                            const float2 hc = H[(size_t)(1 + j) * mm + e];
+                            h.x = fmaf(s_uf[j], hc.x, h.x);
+                            h.y = fmaf(s_uf[j], hc.y, h.y);
+                        }
+                    }
+                    xr[c] = h.y * sc;
+                    xi[c] = -h.x * sc;
                 }
-                S[e] = v;
+                if (r < NP) put8(sm, oBT, plane, NP, r, g, xr, xi, sig, bad);
             }
+            tmem_wait_st();
+            xt_sync();
         }
-        __syncthreads();
-        // Horner in X^p: B = X^p staged once
-        if (q >= 2) tc_stage_b(sm, L, base + (size_t)p * mm_max, m);
-        for (int kb = q - 2; kb >= 0 && !failed; --kb) {
-            if (threadIdx.x < p) coef[threadIdx.x] = (float)s_if[kb * p + threadIdx.x];
-            tc_stage_a(sm, L, S, m);
-            if (!tc_product_out(sm, L, tmem, bar, phase, Sn, m, p, coef, pw)) failed = true;
-            float2* t = S; S = Sn; Sn = t;
-        }
-        if (failed) break;
-        float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
-        if (s > 0 && !tabs.sq_f64) {
-            for (int i = 0; i < s && !failed; ++i) {  // squarings on the tensor cores
-                tc_stage_a(sm, L, S, m);
-                tc_stage_b(sm, L, S, m);
-                if (!tc_product_out(sm, L, tmem, bar, phase, Sn, m, 0, nullptr, nullptr)) failed = true;
-                float2* t = S; S = Sn; Sn = t;
+
+        // last polynomial value of row r, columns 8g..: to U, to the FP64 chain, or into the operands
+        // of the first squaring (A planes, and the identity into the first B^T plane)
+        auto finish8 = [&](int g, const float (&vr)[8], const float (&vi)[8]) {
+            if (s == 0) {
+                if (r < m) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(vr[c], vi[c]);
+                }
+            } else if (sq64) {
+                if (r < m) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        if (8 * g + c < m) D0[(size_t)r * m + 8 * g + c] = make_double2(vr[c], vi[c]);
+                }
+            } else if (r < NP) {
+                put8(sm, oA, plane, NP, r, g, vr, vi, ldexpf(1.f, eQ), bad);
+                uint32_t w[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const uint32_t lo16 = (8 * g + 2 * i == r) ? 0x3C00u : 0u;
+                    const uint32_t hi16 = (8 * g + 2 * i + 1 == r) ? 0x3C00u : 0u;
+                    w[i] = lo16 | (hi16 << 16);
+                }
+                const uint32_t off = (uint32_t)((((r >> 3) * (NP >> 3) + g) << 6) + ((r & 7) << 3)) * 2u;
+                *reinterpret_cast<uint4*>(sm + oBT + off) = make_uint4(w[0], w[1], w[2], w[3]);
+            }
+        };
+
+        // ---- polynomial: Y^T = X^T X^T, then Horner in Y
+        if (q >= 2) {
+            if (threadIdx.x == 0) {
+                tc_fence_after();
+                issue_cprod(aBT, aA, plane, NP, T0re, T0im);
+                mma_commit(&bar);
+            }
+            if (!mma_wait()) { failed = true; break; }
+            {
+                const float fY = ldexpf(1.f, -2 * eX), sigY = ldexpf(1.f, eY), sigS = ldexpf(1.f, eS);
+                const float c1 = s_c[2 * q - 1], c0 = s_c[2 * q - 2];
+                for (int g = half; g < nkg; g += 2) {
+                    float dr[8], di[8], xr[8], xi[8];
+                    ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+                    ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+                    if (r < NP) {
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            dr[c] *= fY;
+                            di[c] *= fY;
+                        }
+                        put8(sm, oBT, plane, NP, r, g, dr, di, sigY, bad);
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            dr[c] = c1 * xr[c] + ((8 * g + c == r && r < m) ? c0 : 0.f);
+                            di[c] = c1 * xi[c];
+                        }
+                        put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
+                    }
+                }
+                xt_sync();
+            }
+            for (int j = q - 2; j >= 0 && !failed; --j) {
+                if (threadIdx.x == 0) {
+                    tc_fence_after();
+                    issue_cprod(aA, aBT, plane, NP, T0re, T0im);
+                    mma_commit(&bar);
+                }
+                if (!mma_wait()) { failed = true; break; }
+                const float f = ldexpf(1.f, -(eS + eY)), sigS = ldexpf(1.f, eS);
+                const float c1 = s_c[2 * j + 1], c0 = s_c[2 * j];
+                for (int g = half; g < nkg; g += 2) {
+                    float dr[8], di[8], xr[8], xi[8];
+                    ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+                    ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        dr[c] = fmaf(dr[c], f, c1 * xr[c]) + ((8 * g + c == r && r < m) ? c0 : 0.f);
+                        di[c] = fmaf(di[c], f, c1 * xi[c]);
+                    }
+                    if (j > 0) {
+                        if (r < NP) put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
+                    } else {
+                        finish8(g, dr, di);
+                    }
+                }
+                xt_sync();
             }
             if (failed) break;
-        } else if (s > 0) {
-            // FP64 squaring chain on the CUDA cores (rare for the norms this path serves)
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) D0[e] = make_double2(S[e].x, S[e].y);
-            __syncthreads();
+        } else {
+            // degree 1: T(X) = I + X
+            for (int g = half; g < nkg; g += 2) {
+                float xr[8], xi[8];
+                ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+#pragma unroll
+                for (int c = 0; c < 8; ++c) xr[c] += (8 * g + c == r && r < m) ? 1.f : 0.f;
+                finish8(g, xr, xi);
+            }
+            xt_sync();
+        }
+
+        // ---- squarings
+        if (s > 0 && !sq64) {
+            // S^T from the product with the identity, into the B^T planes (scale carried over)
+            if (threadIdx.x == 0) {
+                tc_fence_after();
+                issue_ident(aBT, aA, plane, NP, T1re, T1im);
+                mma_commit(&bar);
+            }
+            if (!mma_wait()) { failed = true; break; }
+            for (int g = half; g < nkg; g += 2) {
+                float dr[8], di[8];
+                ld_acc8(R1re + 8 * g, R1im + 8 * g, dr, di);
+                if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
+            }
+            xt_sync();
+            const float f = ldexpf(1.f, -2 * eQ), sigQ = ldexpf(1.f, eQ);
+            for (int i = 1; i <= s && !failed; ++i) {
+                const bool last = i == s;
+                if (threadIdx.x == 0) {
+                    tc_fence_after();
+                    issue_cprod(aA, aBT, plane, NP, T0re, T0im);                // S^2
+                    if (!last) issue_cprod(aBT, aA, plane, NP, T1re, T1im);    // (S^2)^T
+                    mma_commit(&bar);
+                }
+                if (!mma_wait()) { failed = true; break; }
+                for (int g = half; g < nkg; g += 2) {
+                    float dr[8], di[8];
+                    ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        dr[c] *= f;
+                        di[c] *= f;
+                    }
+                    if (last) {
+                        if (r < m) {
+#pragma unroll
+                            for (int c = 0; c < 8; ++c)
+                                if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(dr[c], di[c]);
+                        }
+                    } else {
+                        float tr[8], ti[8];
+                        ld_acc8(R1re + 8 * g, R1im + 8 * g, tr, ti);
+                        if (r < NP) {
+                            put8(sm, oA, plane, NP, r, g, dr, di, sigQ, bad);
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                tr[c] *= f;
+                                ti[c] *= f;
+                            }
+                            put8(sm, oBT, plane, NP, r, g, tr, ti, sigQ, bad);
+                        }
+                    }
+                }
+                xt_sync();
+            }
+            if (failed) break;
+        } else if (sq64) {
+            // FP64 squaring chain on the CUDA cores
             double2* Da = D0;
             double2* Db = D1;
             for (int i = 0; i < s; ++i) {
@@ -228,51 +493,80 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                     Db[e] = acc;
                 }
                 __syncthreads();
-                double2* t = Da; Da = Db; Db = t;
+                double2* t = Da;
+                Da = Db;
+                Db = t;
             }
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) S[e] = make_float2((float)Da[e].x, (float)Da[e].y);
+            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = make_float2((float)Da[e].x, (float)Da[e].y);
             __syncthreads();
         }
-        for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
-        __syncthreads();
     }
+    if (bad) atomicOr(P.status, ST_RANGE);
     if (failed) {
+        // the commit never arrived: give the MMAs in flight another bounded wait before freeing TMEM
         if (threadIdx.x == 0) {
             atomicOr(P.status, ST_TIMEOUT);
-            mbar_wait_bounded(bar, phase, TC_WAIT_NS);
+            mbar_wait_bounded(&bar, phase, XT_WAIT_NS);
         }
         __syncthreads();
     }
     tc_fence_before();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, TC_TMEM_COLS);
+    if (warp == 0) tmem_dealloc(tmem, tmem_cols);
+}
+
+// Launch shape of a class whose largest block is m_max: dynamic shared memory (raised, if need be,
+// so that no more CTAs share an SM than its tensor memory holds), TMEM columns, CTAs per SM.
+struct XtConfig {
+    size_t smem;
+    uint32_t tmem_cols;
+    int per_sm;
+};
+
+XtConfig xt_config(int m_max) {
+    XtConfig c{};
+    const int NP = xt_pad16(m_max);
+    c.smem = xt_smem(NP);
+    c.tmem_cols = 4u * (uint32_t)xt_cs(NP);
+    const int by_tmem = (int)(512u / c.tmem_cols);
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, expm_tc_kernel);
+    const size_t per_sm_smem = 233472, reserved = 1024;  // 228 KB per SM, 1 KB reserved per CTA
+    const size_t need = c.smem + fa.sharedSizeBytes + reserved;
+    int by_smem = (int)(per_sm_smem / need);
+    const int by_regs = fa.numRegs > 0 ? 65536 / (fa.numRegs * XT_THREADS) : 1;
+    int k = std::min(std::min(by_tmem, by_smem), std::max(by_regs, 1));
+    if (k < 1) k = 1;
+    if (by_smem > k) {  // raise the request until only k CTAs fit
+        const size_t want = per_sm_smem / (size_t)(k + 1) + 16;
+        if (want > fa.sharedSizeBytes + reserved) c.smem = std::max(c.smem, want - fa.sharedSizeBytes - reserved);
+    }
+    c.per_sm = k;
+    return c;
 }
 
 }  // namespace
 
-int expm_tc_supported(int prec, int m) { return prec != QOC_PREC_F64 && m >= 1 && m <= TC_MAXM; }
+int expm_tc_supported(int prec, int m) { return prec != QOC_PREC_F64 && m >= 1 && m <= XT_MAXM; }
 
-size_t expm_tc_smem(int m_max) {
-    TcLayout L{tc_pad16(m_max), tc_pad16(m_max)};
-    return L.total();
-}
+size_t expm_tc_slot_bytes(int m_max) { return (size_t)2 * m_max * m_max * sizeof(double2); }
 
-int expm_tc_grid_limit() {
+int expm_tc_grid_limit(int m_max) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    return sms;  // one CTA per SM (shared memory and half of TMEM each)
+    return sms * xt_config(m_max).per_sm;
 }
 
 int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                    const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
                    int grid, cudaStream_t st) {
-    TcLayout L{tc_pad16(m_max), tc_pad16(m_max)};
-    const size_t smem = L.total();
-    if (cudaFuncSetAttribute(expm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    if (m_max > XT_MAXM) return -1;
+    const XtConfig c = xt_config(m_max);
+    if (cudaFuncSetAttribute(expm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) != cudaSuccess)
         return -1;
-    expm_tc_kernel<<<grid, TC_THREADS, smem, st>>>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes,
-                                                   m_max, L);
+    expm_tc_kernel<<<grid, XT_THREADS, c.smem, st>>>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes,
+                                                     m_max, c.tmem_cols);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

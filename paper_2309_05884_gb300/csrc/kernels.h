@@ -15,6 +15,7 @@ struct ExpmTables {
     int n_deg;          // degrees allowed (prefix of the table)
     double theta_cap;   // largest norm the polynomial is evaluated at; larger norms are scaled
     int sq_f64;         // 1: squaring chain in FP64; 0: in the working precision
+    double theta_odd[16];  // theta_odd[q-1]: norm bound of the odd Taylor degree 2q-1 (tensor-core kernel)
 };
 
 // ---- expm.cu
@@ -38,7 +39,8 @@ int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, 
 
 // ---- expm_tc.cu (tcgen05 tensor cores, FP16-split products; FP32 plans, m <= 112)
 int expm_tc_supported(int prec, int m);
-int expm_tc_grid_limit();
+int expm_tc_grid_limit(int m_max);
+size_t expm_tc_slot_bytes(int m_max);
 int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                    const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
                    int grid, cudaStream_t st);

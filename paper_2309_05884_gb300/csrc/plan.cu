@@ -301,8 +301,8 @@ int build_classes(qoc_plan* p) {
         c.n_items = (long long)cls_items.size() - c.item_off;
         const long long max_items = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
         if (c.kind == 2) {
-            c.grid = (int)std::max<long long>(1, std::min<long long>(max_items, expm_tc_grid_limit()));
-            c.slot_bytes = align_up(expm_slot_bytes(1, c.m_max), 256);
+            c.grid = (int)std::max<long long>(1, std::min<long long>(max_items, expm_tc_grid_limit(c.m_max)));
+            c.slot_bytes = align_up(expm_tc_slot_bytes(c.m_max), 256);
             p->expm_scratch = std::max(p->expm_scratch, c.slot_bytes * (size_t)c.grid);
         } else if (c.kind == 1) {
             const long long groups = (max_items + c.per_warp - 1) / c.per_warp;
@@ -573,6 +573,7 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     const int degs[9] = {2, 4, 6, 9, 12, 16, 20, 25, 30};
     const double unit = o.prec == QOC_PREC_F64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
     for (int i = 0; i < 9; ++i) p->tabs.theta[i] = theta_for(degs[i], unit);
+    for (int q = 1; q <= 16; ++q) p->tabs.theta_odd[q - 1] = theta_for(2 * q - 1, unit);
     if (o.prec == QOC_PREC_F64) {
         p->tabs.n_deg = 9;
         p->tabs.theta_cap = p->tabs.theta[8];
@@ -711,6 +712,8 @@ int qoc_plan_sync_status(qoc_plan* p, void* stream) {
     if (st & ST_NAN_PULSE) return set_error(QOC_EINVAL, "non-finite pulse value");
     if (st & ST_SQUARING_CAP) return set_error(QOC_EUNSUPPORTED, "a slice needed more squarings than max_squarings");
     if (st & ST_SERIES_CAP) return set_error(QOC_EUNSUPPORTED, "a slice's norm is beyond the gradient series' range");
+    if (st & ST_RANGE)
+        return set_error(QOC_EUNSUPPORTED, "a tensor-core expm operand left the FP16-split range (non-Hermitian H?)");
     return QOC_OK;
 }
 

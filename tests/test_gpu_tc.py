@@ -85,3 +85,80 @@ def test_tensor_core_expm_matches_tiled_and_oracle(prec):
     gc = g_c.cpu().numpy()
     assert np.linalg.norm(gc - gref) / np.linalg.norm(gref) <= 1e-5
     assert np.linalg.norm(gc - g_t.cpu().numpy()) / np.linalg.norm(gref) <= 1e-5
+
+
+def _propagator_errors(system, prec, u, ckpt=0):
+    """Max |U - U_oracle| over every slice and block, for the tensor-core kernel and the tiled one.
+    The oracle exponentiates the basis builder's block Hamiltonians by eigendecomposition in FP64."""
+    from oracle import grape as gr
+    from paper_2309_05884_gb300 import api
+    B = api.Basis(system)
+    plan = api.Plan(B, system.N, system.tau, prec=prec)
+    ut = torch.from_numpy(np.ascontiguousarray(u)).to(DEV)
+    U_t = plan.expm(ut).cpu().numpy()
+    plan.set_expm_rules([(112, 2, 0)])
+    assert all(c[0] == 2 for c in plan.expm_classes())
+    U_c = plan.expm(ut).cpu().numpy()
+    torch.cuda.synchronize()
+    plan.sync_status()
+    off, e_c, e_t = 0, 0.0, 0.0
+    for b in plan.active_blocks():
+        m = B.blocks[b][1]
+        h0, hc = B.block_matrices(b)
+        Uref = gr.propagators(dict(h0=h0, hc=list(hc)), u, system.tau)
+        n = system.N * m * m
+        e_c = max(e_c, np.abs(U_c[off:off + n].reshape(system.N, m, m) - Uref).max())
+        e_t = max(e_t, np.abs(U_t[off:off + n].reshape(system.N, m, m) - Uref).max())
+        off += n
+    return e_c, e_t
+
+
+@pytest.mark.parametrize("case", ["tiny_norm", "moderate", "squarings_tc", "squarings_fp64", "small_blocks",
+                                  "mid_blocks"])
+def test_tensor_core_propagators_match_oracle(case):
+    # tiny_norm: degree 1 (no product); moderate: Horner in X^2 only; squarings_tc: |tau H| ~ 50 with
+    # the squarings on the tensor cores (FP32 plan); squarings_fp64: the same norms with the FP64
+    # squaring chain; small/mid blocks: several CTAs per SM (operand sizes 16..48)
+    from paper_2309_05884_gb300 import inputs as I
+    if case == "tiny_norm":
+        s, prec, tol = I.xxz_ring(8, 4e-5, 4), "f32", 2e-6
+    elif case == "moderate":
+        s, prec, tol = I.xxz_ring(10, 0.5, 10), "f32", 1e-5
+    elif case == "squarings_tc":
+        s, prec, tol = I.xxz_ring(8, 20.0, 5), "f32_all", 2e-4
+    elif case == "squarings_fp64":
+        s, prec, tol = I.xxz_ring(8, 20.0, 5), "f32", 2e-5
+    elif case == "small_blocks":
+        s, prec, tol = I.sn_allpairs(12, 1.0, 0.5, 3.0, 12), "f32_all", 2e-5
+    else:
+        s, prec, tol = I.xxz_ring(8, 2.0, 12), "f32_all", 2e-5
+    u = I.pulses_normal(17, s.N, s.n_ctrl) if s.n_ctrl == 3 else I.pulses_uniform(17, s.N, s.n_ctrl)
+    e_c, e_t = _propagator_errors(s, prec, u)
+    assert e_c <= tol, (e_c, e_t)
+    # and within the split's precision of the FP32 CUDA-core kernel on the same slices: two FP16
+    # halves carry 22 significant bits against FP32's 24, and the dropped lo*lo term is of the same
+    # order, so up to about 8x its error
+    assert e_c <= max(8 * e_t, tol / 4), (e_c, e_t)
+
+
+def test_tensor_core_expm_in_checkpoint_windows():
+    # the windowed launches (slice windows of one problem) give the gradient of the whole-problem launch
+    from paper_2309_05884_gb300 import api
+    from paper_2309_05884_gb300 import inputs as I
+    s = I.xxz_ring(8, 4.0, 40)
+    psi0, psif = I.random_state(311, 256), I.random_state(312, 256)
+    B = api.Basis(s)
+    b0, bf = B.state_to_blocks(psi0), B.state_to_blocks(psif)
+    act = B.active_copies(b0, bf)
+    d0, df = api.to_device(b0, DEV), api.to_device(bf, DEV)
+    u = torch.from_numpy(I.pulses_normal(19, s.N, 3)).to(DEV)
+    res = []
+    for seg in (0, 7):
+        plan = api.Plan(B, s.N, s.tau, prec="f32_all", active=act, ckpt_segment=seg)
+        plan.set_expm_rules([(112, 2, 0)])
+        o, g = plan.fidelity_and_grad(u, d0, df)
+        torch.cuda.synchronize()
+        plan.sync_status()
+        res.append((o.cpu().numpy(), g.cpu().numpy()))
+    assert abs(res[0][0][0] - res[1][0][0]) <= 1e-12
+    assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * max(1.0, np.abs(res[0][1]).max())
