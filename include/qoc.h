@@ -234,6 +234,17 @@ int qoc_optimize_pulses(qoc_plan* plan, double* u, const double* psi0, const dou
                         void* stream);
 
 /* ---------------------------------------------------------------- tuning */
+/* Sweep kernel of the forward/backward passes (Sec. II.A, Eq. exppropagator; costates through
+ * U_k^dagger as in Appendix B).  cl = 2, 4 or 8 splits each (direction, block) chain over a
+ * thread-block cluster of cl CTAs (rows of U_k per CTA, state exchanged through distributed shared
+ * memory each step); 0 runs one CTA per chain; -1 restores the automatic choice made at plan
+ * creation (clusters when every chain's cluster can be resident at once and blocks have m >= 24).
+ * Returns QOC_EINVAL for other values, QOC_EUNSUPPORTED if the cluster buffers of the plan's largest
+ * block do not fit in shared memory.  The paper has no counterpart: it is a launch-shape choice. */
+int qoc_plan_set_sweep_cluster(qoc_plan* plan, int cl);
+/* Current cluster size of the sweeps (0: one CTA per chain). */
+int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
+
 /* Kernel choice of the batched exponentials (Sec. II.A, Eq. exppropagator, as in qoc_expm_blocks):
  * rule i applies to blocks of size m <= m_max[i] (rules are tried in increasing m_max; the first
  * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =

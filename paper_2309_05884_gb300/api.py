@@ -297,6 +297,16 @@ class Plan:
             self.workspace_bytes = nbytes.value
             self._ws = None
 
+    def set_sweep_cluster(self, cl: int) -> None:
+        """Sweep kernel: cl = 2, 4 or 8 CTAs per chain in a thread-block cluster, 0 one CTA per
+        chain, -1 the automatic choice."""
+        L.check(self.lib.qoc_plan_set_sweep_cluster(self.handle, cl), "qoc_plan_set_sweep_cluster")
+
+    def sweep_cluster(self) -> int:
+        n = C.c_int()
+        L.check(self.lib.qoc_plan_sweep_cluster(self.handle, C.byref(n)), "qoc_plan_sweep_cluster")
+        return n.value
+
     def expm_classes(self):
         """[(kind, param, per_warp, m_max, n_blocks)] of the plan's exponential launches."""
         n = C.c_int()

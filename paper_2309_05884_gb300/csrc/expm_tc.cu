@@ -17,8 +17,8 @@
 // Layouts.  A product D = A B takes A as an M x K operand (rows of A, K-major) and B as its transpose
 // B^T (rows of B^T, K-major), both in 8 x 16-byte core matrices without swizzle.  A transposed copy of
 // a result comes from the same product with the operands swapped, (AB)^T = B^T A^T, so every
-// epilogue writes rows: Y^T for the Horner steps, (S^2)^T beside S^2 in the squarings, and S^T (from
-// a product with the identity) before the first squaring.
+// epilogue writes rows: Y^T for the Horner steps, (S^2)^T beside S^2 in the squarings; X^T and, before
+// the first squaring, S^T come from a product with the identity, so H is read once per slice.
 //
 // Shared memory: four B^T planes (re hi, re lo, im hi, im lo; NP x NP halves each, NP = m rounded up
 // to 16), four A planes, then slack: an MMA with M = 128 reads 128 rows of its A operand, so the rows
@@ -81,6 +81,19 @@ __device__ __forceinline__ void put8(unsigned char* sm, uint32_t grp, uint32_t p
     split8(im, sig, hi, lo, bad);
     *reinterpret_cast<uint4*>(sm + grp + 2 * plane + off) = hi;
     *reinterpret_cast<uint4*>(sm + grp + 3 * plane + off) = lo;
+}
+
+// Row r, columns 8g..8g+7 of the identity into one FP16 plane (at byte offset pl).
+__device__ __forceinline__ void put_ident8(unsigned char* sm, uint32_t pl, int NP, int r, int g) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const uint32_t lo16 = (8 * g + 2 * i == r) ? 0x3C00u : 0u;  // FP16 1.0
+        const uint32_t hi16 = (8 * g + 2 * i + 1 == r) ? 0x3C00u : 0u;
+        w[i] = lo16 | (hi16 << 16);
+    }
+    const uint32_t off = (uint32_t)((((r >> 3) * (NP >> 3) + g) << 6) + ((r & 7) << 3)) * 2u;
+    *reinterpret_cast<uint4*>(sm + pl + off) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 
 // Read columns col..col+7 of the re and im planes of an accumulator (one TMEM lane per thread).
@@ -271,53 +284,64 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
         const bool sq64 = s > 0 && tabs.sq_f64;
         float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
 
-        // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1, columns into B^T
+        // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1 (one read of H)
         {
             const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
             const float sc = s_sc, sig = ldexpf(1.f, eX);
+            const bool rin = r < m;
             for (int g = half; g < nkg; g += 2) {
-                float xr[8], xi[8];
+                float2 h[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int col = 8 * g + c;
-                    float2 h = make_float2(0.f, 0.f);
-                    if (r < m && col < m) {
-                        const size_t e = (size_t)r * m + col;
-                        h = H[e];
-                        for (int j = 0; j < P.nc; ++j) {
-                            const float2 hc = H[(size_t)(1 + j) * mm + e];
-                            h.x = fmaf(s_uf[j], hc.x, h.x);
-                            h.y = fmaf(s_uf[j], hc.y, h.y);
+                    h[c] = (rin && col < m) ? H[(size_t)r * m + col] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {  // every load of a matrix's 8 entries in flight together
+                    if (j < P.nc) {
+                        const float2* Hj = H + (size_t)(1 + j) * mm + (size_t)r * m;
+                        const float uj = s_uf[j];
+#pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            const int col = 8 * g + c;
+                            if (rin && col < m) {
+                                const float2 hc = Hj[col];
+                                h[c].x = fmaf(uj, hc.x, h[c].x);
+                                h[c].y = fmaf(uj, hc.y, h[c].y);
+                            }
                         }
                     }
-                    xr[c] = h.y * sc;
-                    xi[c] = -h.x * sc;
                 }
-                if (r < NP) put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
-                tmem_st8(R1re + 8 * g, xr);
-                tmem_st8(R1im + 8 * g, xi);
-            }
-            for (int g = half; g < nkg; g += 2) {
                 float xr[8], xi[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const int row = 8 * g + c;  // column r of X is row r of X^T
-                    float2 h = make_float2(0.f, 0.f);
-                    if (r < m && row < m) {
-                        const size_t e = (size_t)row * m + r;
-                        h = H[e];
-                        for (int j = 0; j < P.nc; ++j) {
-                            const float2 hc = H[(size_t)(1 + j) * mm + e];
-                            h.x = fmaf(s_uf[j], hc.x, h.x);
-                            h.y = fmaf(s_uf[j], hc.y, h.y);
-                        }
-                    }
-                    xr[c] = h.y * sc;
-                    xi[c] = -h.x * sc;
+                    xr[c] = h[c].y * sc;
+                    xi[c] = -h[c].x * sc;
                 }
-                if (r < NP) put8(sm, oBT, plane, NP, r, g, xr, xi, sig, bad);
+                if (r < NP) {
+                    put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
+                    if (q >= 2) put_ident8(sm, oBT, NP, r, g);  // for the transpose below
+                }
+                tmem_st8(R1re + 8 * g, xr);
+                tmem_st8(R1im + 8 * g, xi);
             }
             tmem_wait_st();
+            xt_sync();
+        }
+        // X^T (rows into the B^T planes), needed by the Horner steps: the product I X on the tensor
+        // cores, exactly the split sum of each entry, replaces a second, transposed read of H
+        if (q >= 2) {
+            if (threadIdx.x == 0) {
+                tc_fence_after();
+                issue_ident(aBT, aA, plane, NP, T0re, T0im);
+                mma_commit(&bar);
+            }
+            if (!mma_wait()) { failed = true; break; }
+            for (int g = half; g < nkg; g += 2) {
+                float dr[8], di[8];
+                ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+                if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
+            }
             xt_sync();
         }
 
@@ -338,15 +362,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                 }
             } else if (r < NP) {
                 put8(sm, oA, plane, NP, r, g, vr, vi, ldexpf(1.f, eQ), bad);
-                uint32_t w[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const uint32_t lo16 = (8 * g + 2 * i == r) ? 0x3C00u : 0u;
-                    const uint32_t hi16 = (8 * g + 2 * i + 1 == r) ? 0x3C00u : 0u;
-                    w[i] = lo16 | (hi16 << 16);
-                }
-                const uint32_t off = (uint32_t)((((r >> 3) * (NP >> 3) + g) << 6) + ((r & 7) << 3)) * 2u;
-                *reinterpret_cast<uint4*>(sm + oBT + off) = make_uint4(w[0], w[1], w[2], w[3]);
+                put_ident8(sm, oBT, NP, r, g);
             }
         };
 

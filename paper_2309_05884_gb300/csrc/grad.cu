@@ -75,7 +75,7 @@ template <class T>
 __global__ void __launch_bounds__(GRAD_THREADS)
 grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, const cx<T>* __restrict__ psi_st,
             const cx<T>* __restrict__ lam_st, double2* __restrict__ partial, char* __restrict__ scratch,
-            size_t slot_bytes, int a_in_smem, int max_m) {
+            size_t slot_bytes, int a_in_smem, int max_m, int fast_m) {
     constexpr int PM = GradCfg<T>::P;
     constexpr int CG = GradCfg<T>::CG;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -144,6 +144,10 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
         }
         __syncthreads();
         if (s_sub >= REV_MIN_SUB) {  // large-norm slice: the reverse-mode kernel (grad_rev.cu) owns it
+            __syncthreads();
+            continue;
+        }
+        if (s_sub == 0 && m <= fast_m) {  // unsplit slice of a register-sized block: grad_fast.cu owns it
             __syncthreads();
             continue;
         }
@@ -464,13 +468,13 @@ int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_stor
         cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<double><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-17, 3.8, u, (const double2*)psi_store,
                                                            (const double2*)lam_store, partial, scratch, slot_bytes,
-                                                           grad_mode_of<double>(max_m), max_m);
+                                                           grad_mode_of<double>(max_m), max_m, 0);
     } else {
         const size_t sm = grad_smem<float>(max_m);
         cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-9, 3.0, u, (const float2*)psi_store,
                                                           (const float2*)lam_store, partial, scratch, slot_bytes,
-                                                          grad_mode_of<float>(max_m), max_m);
+                                                          grad_mode_of<float>(max_m), max_m, grad_fast_max_m(P.prec));
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

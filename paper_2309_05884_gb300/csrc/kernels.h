@@ -37,6 +37,11 @@ int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, 
                      const int2* items, long long n_items, int MP, int per_warp, void* Uout, int grid,
                      cudaStream_t st);
 
+// ---- grad_fast.cu (exact slice derivatives, FP32, m <= 128, unsplit slices; A in registers)
+int grad_fast_max_m(int prec);
+int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
+                     int max_m, int grid, cudaStream_t st);
+
 // ---- expm_tc.cu (tcgen05 tensor cores, FP16-split products; FP32 plans, m <= 112)
 int expm_tc_supported(int prec, int m);
 int expm_tc_grid_limit(int m_max);
@@ -49,6 +54,12 @@ int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, co
 // Forward (psi_{i+1} = U_i psi_i) and/or backward (lam_i = U_i^dagger lam_{i+1}) sweeps over the
 // current slice window of every active block, one CTA per (direction, block); dirs: 1 = forward,
 // 2 = backward, 3 = both.  Boundary vectors are [block][copy][m] arrays in the working precision.
+// ---- sweep_cluster.cu (each chain over a thread-block cluster, DSMEM exchange per step)
+int sweep_cluster_size(int prec, int nb, int max_m, int max_c);
+int sweep_cluster_fits(int prec, int max_m, int max_c, int CL);
+int launch_sweeps_cluster(const DevPlan& P, const void* U, const void* fwd_init, void* fwd_out, const void* bwd_init,
+                          void* bwd_out, void* psi_store, void* lam_store, int dirs, int max_m, int max_c, int CL,
+                          cudaStream_t st);
 int launch_sweeps(const DevPlan& P, const void* U, const void* fwd_init, void* fwd_out, const void* bwd_init,
                   void* bwd_out, void* psi_store, void* lam_store, int dirs, int max_m, int max_c, cudaStream_t st);
 // dst (boundary layout, working precision) <- the caller's block state (complex128).

@@ -79,6 +79,8 @@ struct qoc_plan {
     std::vector<ExpmRule> rules;
     size_t expm_scratch = 0;
     int grad_grid = 0;
+    int gf_grid = 0;  // register-tile gradient kernel
+    int sweep_cl = 0;  // cluster size of the sweeps (0: one CTA per chain)
     size_t grad_slot = 0;
     int rev_grid = 0;
     size_t rev_slot = 0;
@@ -197,8 +199,11 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
 int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char* fwd_in, char* fwd_out,
                const char* bwd_in, char* bwd_out, cudaStream_t st) {
     const DevPlan P = p->dev(k0, nk);
-    const int rc = launch_sweeps(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
-                                 ws + p->off_lam, dirs, p->max_m, p->max_c, st);
+    const int rc = p->sweep_cl > 0
+                       ? launch_sweeps_cluster(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
+                                               ws + p->off_lam, dirs, p->max_m, p->max_c, p->sweep_cl, st)
+                       : launch_sweeps(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
+                                       ws + p->off_lam, dirs, p->max_m, p->max_c, st);
     if (rc == -2) return set_error(QOC_EUNSUPPORTED, "block states do not fit in shared memory");
     if (rc != 0) return cuda_fail(cudaGetLastError(), "sweep launch");
     return QOC_OK;
@@ -211,6 +216,9 @@ int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
                                        p->grad_slot, p->max_m, p->grad_grid, st);
     if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
     if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
+    if (launch_grad_fast(P, u, ws + p->off_psi, ws + p->off_lam, reinterpret_cast<double2*>(ws + p->off_partial),
+                         p->max_m, p->gf_grid, st) != 0)
+        return cuda_fail(cudaGetLastError(), "gradient launch (register tiles)");
     if (P.grad_mode == 0) {
         // large-norm slices: reverse-mode kernel, one launch per size class with that class's tile
         for (const auto& c : p->classes) {
@@ -596,6 +604,13 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     p->grad_slot = align_up(grad_slot_bytes(wp, p->max_m), 256);
     const long long grad_items = p->nseg == 1 ? (long long)p->items.size() : (long long)p->seg * p->nb;
     p->grad_grid = (int)std::min<long long>(grad_items, grad_grid_limit(wp, p->max_m));
+    p->sweep_cl = sweep_cluster_size(wp, p->nb, p->max_m, p->max_c);
+    {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        p->gf_grid = (int)std::max<long long>(1, std::min<long long>(grad_items, sms));
+    }
     // reverse-mode kernel for large-norm slices: one scratch slot per CTA, at most 256 MiB in total
     {
         int dev = 0, sms = 0;
@@ -755,11 +770,32 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     // gathers, one expm launch per size class, sweeps, overlap, slice derivatives, reduction
     // (+ the iteration counter when optimising); propagate: gather, expm, sweep, memset, store
     const int ncls = (int)p->classes.size();
+    // register-tile derivative launches per gradient pass (FP32 plans): one per size range used
+    const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? (p->max_m > 64 ? 2 : 1) : 0;
     if (p->nseg == 1)
-        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + ncls + 1 : 1 + ncls + 1 + 1;
+        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + ncls + 1 : 1 + ncls + 1 + 1;
     else
-        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (2 * ncls + 2) + 1
+        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (2 * ncls + 2 + gfl) + 1
                               : 1 + p->nseg * (ncls + 1) + 1;
+    return QOC_OK;
+}
+
+int qoc_plan_set_sweep_cluster(qoc_plan* p, int cl) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    if (cl == -1) {
+        p->sweep_cl = sweep_cluster_size(p->opts.prec, p->nb, p->max_m, p->max_c);
+        return QOC_OK;
+    }
+    if (cl != 0 && cl != 2 && cl != 4 && cl != 8) return set_error(QOC_EINVAL, "cluster size must be -1, 0, 2, 4 or 8");
+    if (cl > 0 && !sweep_cluster_fits(p->opts.prec, p->max_m, p->max_c, cl))
+        return set_error(QOC_EUNSUPPORTED, "cluster sweep buffers do not fit in shared memory");
+    p->sweep_cl = cl;
+    return QOC_OK;
+}
+
+int qoc_plan_sweep_cluster(const qoc_plan* p, int* cl) {
+    if (!p || !cl) return set_error(QOC_EINVAL, "null argument");
+    *cl = p->sweep_cl;
     return QOC_OK;
 }
 
