@@ -41,6 +41,20 @@ FP32_PEAK_NOTE = "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max S
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+def measured_peaks():
+    """HBM and dense tensor peaks from MEASURED_PEAKS.json (the profiling recipe's fallback if absent)."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "hbm_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "tensor_tflops": float(d["bf16_tflops"]),
+                "tensor_note": "measured dense BF16 burst rate (MEASURED_PEAKS.json bf16_tflops); FP16 x 1"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "hbm_note": "fallback 6.8 TB/s", "tensor_tflops": 1900.0,
+                "tensor_note": "fallback 1.9 PFLOP/s BF16 burst; FP16 x 1"}
+
+
 def workload():
     s = I.c2_system()
     psi0 = I.random_state(SEED_PSI0, 2 ** s.n)
@@ -189,6 +203,10 @@ class D10:
         self._s, self._p0, self._pf, self._u = s, psi0_full, psif_full, u0
         return plan, u0, b0, bf
 
+    def sweep_bytes(self, plan):
+        # FP32 complex propagators (8 B per element), read by the forward and the backward sweep
+        return 2 * 8 * plan.export_elems()
+
     def cpu_rate(self):
         Ns = 250
         rate, secs = cpu_oracle_rate(self._s, self._p0, self._pf, self._u, Ns)
@@ -213,6 +231,9 @@ class SnBatch:
         u0 = np.concatenate([I.pulses_uniform(p.seed, p.N, 2) for p in probs])
         plan = api.Plan(bases, [p.N for p in probs], [SN_T / p.N for p in probs], prec=self.prec)
         return plan, u0, b0, bf
+
+    def sweep_bytes(self, plan):
+        return 2 * 8 * sum(p.N * (p.n + 1) ** 2 for p in self._probs)
 
     def cpu_rate(self):
         from oracle import grape as gr
@@ -339,18 +360,48 @@ def run_ours(args, rank, world):
     value = world * wl.problems * args.steps / (total_ms / 1e3)
     ph = np.mean(np.array(phases), axis=0)
 
-    # roofline of the batched exponential: algorithmic flops per launch set (complex MAC = 8 flop)
-    flops_poly = 8.0 * counts[0] / args.steps
-    flops_sq = 8.0 * counts[1] / args.steps
-    expm_ms = float(ph[0])
-    achieved = (flops_poly + flops_sq) / (expm_ms * 1e-3) / 1e12
+    # rooflines per phase, from algorithmic work per call (complex multiply-add = 8 flop) and the
+    # in-step CUDA-event phase times; the line's "roofline" is the phase that takes longest
+    peaks = measured_peaks()
+    n = args.steps
     phase_ms = {"expm": float(ph[0]), "sweeps": float(ph[1]), "overlap": float(ph[2]),
                 "slice_derivatives": float(ph[3]), "reduce_update": float(ph[4])}
-    roof = {"bound": "alu", "kernel": "batched expm (all launches of one call)",
-            "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-            "traffic": None, "peak_source": FP32_PEAK_NOTE,
-            "flops_per_launch": flops_poly + flops_sq, "squaring_flops": flops_sq, "phase_ms": phase_ms,
-            "dominant_phase": max(phase_ms, key=phase_ms.get)}
+    classes = plan.expm_classes()
+    on_tc = any(c[0] == 2 for c in classes)
+    expm_flop = 8.0 * (counts[0] + counts[1]) / n
+    roofs = {}
+    if on_tc:
+        # kind::f16 MMAs: the measured BF16 dense rate (FP16 has the same nominal rate)
+        tc_peak, tc_src = peaks["tensor_tflops"], peaks["tensor_note"]
+        roofs["expm"] = {"bound": "tensor", "kernel": "expm_tc_kernel (tcgen05, FP16 hi/lo split)",
+                         "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": tc_peak,
+                         "unit": "TFLOP/s", "peak_source": tc_src,
+                         "flops_per_launch": expm_flop,
+                         "note": "algorithmic complex-FP32 flop (8 m^3 per product); the split issues 12 "
+                                 "real FP16 products per complex product on 16-padded operands"}
+    else:
+        roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles)",
+                         "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_launch": expm_flop}
+    grad_flop = 8.0 * counts[3] / n
+    roofs["slice_derivatives"] = {
+        "bound": "alu", "kernel": "grad_fast_kernel (register tiles, FP32 FMA)",
+        "achieved": grad_flop / (phase_ms["slice_derivatives"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
+        "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_launch": grad_flop,
+        "note": "series work (c (3P+1) + n_ctrl) m^2 complex multiply-adds per (slice, block) item"}
+    sweep_bytes = wl.sweep_bytes(plan)
+    if sweep_bytes:
+        roofs["sweeps"] = {"bound": "hbm", "kernel": "sweep_cluster_kernel" if plan.sweep_cluster() else "sweep_kernel",
+                           "achieved": sweep_bytes / (phase_ms["sweeps"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                           "unit": "GB/s", "peak_source": peaks["hbm_note"], "bytes_per_launch": sweep_bytes,
+                           "note": "every stored propagator read once forward and once backward"}
+    for r in roofs.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["traffic"] = None
+    dominant = max((k for k in roofs), key=lambda k: phase_ms[k])
+    roof = dict(roofs[dominant])
+    roof["phase"] = dominant
+    roof["phase_ms"] = phase_ms
 
     # end to end through the C ABI with host buffers: H2D of u and both states, D2H of F and dF/du
     u_h = torch.from_numpy(u0.copy()).pin_memory()
@@ -397,6 +448,7 @@ def run_ours(args, rank, world):
                        "expm_kernels": [list(c) for c in plan.expm_classes()],
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "roofline": roof,
+            "rooflines": roofs,
             "cpu_baseline": cpu,
             "e2e": {"value": world * wl.problems * e2e_steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

@@ -250,7 +250,12 @@ int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
  * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =
  * by size); kind 1 = warp-packed kernel (m <= 32 FP32, <= 16 FP64, not with QOC_PREC_F32), param =
  * matrices per warp (0 = as many as fit); kind 2 = tcgen05 tensor-core kernel (FP32 plans, m <= 112;
- * products as in qoc_tc_cgemm).  Blocks no rule covers use the tiled kernel.  The plan's
+ * products as in qoc_tc_cgemm), param 0 = only the slices that need no squaring (the block's other
+ * slices run on the tiled kernel in a second launch), param 1 = every slice.  Blocks no rule covers
+ * use the tiled kernel.  At plan creation FP32 plans use kind 2, param 0 for blocks of 25..112
+ * states and the tiled kernel for the rest; FP64 plans use the tiled kernel.  A tensor-core product
+ * (two FP16 halves per operand, all four split products) errs up to about 2x an FP32 one, which
+ * the squarings of large-norm slices would amplify.   The plan's
  * workspace size may change: query qoc_plan_workspace_bytes again.  An autotuner times candidate
  * rules (paper_2309_05884_gb300/autotune.py). */
 int qoc_plan_set_expm_rules(qoc_plan* plan, int n_rules, const int* m_max, const int* kind, const int* param);
@@ -265,8 +270,11 @@ int qoc_plan_expm_classes(const qoc_plan* plan, int max_out, int* n_classes, int
  *   [0] assembly + batched expm, [1] forward/backward sweeps, [2] overlap, [3] slice derivatives,
  *   [4] gradient reduction / update.
  * Work counters (reset by enabling): counts[0] = sum over (slice, block) items of m^3 times the
- * polynomial products taken (working precision), counts[1] = sum of m^3 times the FP64 squarings,
- * counts[2] = (slice, block) items exponentiated. */
+ * polynomial products taken (working precision), counts[1] = sum of m^3 times the squarings,
+ * counts[2] = (slice, block) items exponentiated, counts[3] = complex multiply-adds of the exact
+ * slice-derivative series done by the register-tile kernel (FP32 plans, unsplit slices): per item
+ * (c (3P + 1) + n_ctrl) m^2 for c copies and series length P (2P matrix-vector products per copy,
+ * the (P+1)-term M tile, the contraction with each Hc_j). */
 int qoc_plan_set_profiling(qoc_plan* plan, int on);
 int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
 int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);

@@ -278,9 +278,10 @@ class Plan:
         return list(ms)
 
     def work_counts(self) -> List[int]:
-        """[sum m^3 * polynomial products, sum m^3 * FP64 squarings, items] since profiling was enabled."""
-        out = (C.c_longlong * 3)()
-        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 3), "qoc_plan_work_counts")
+        """[sum m^3 * polynomial products, sum m^3 * squarings, items, complex multiply-adds of the
+        register-tile derivative series] since profiling was enabled."""
+        out = (C.c_longlong * 4)()
+        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 4), "qoc_plan_work_counts")
         return list(out)
 
     def set_expm_rules(self, rules) -> None:

@@ -22,7 +22,7 @@ template <class T, int R>
 __global__ void __launch_bounds__(GEMM_THREADS)
 expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int* __restrict__ cls_blocks,
             int n_cls, const int2* __restrict__ cls_items, long long n_cls_items, void* __restrict__ Uout,
-            char* __restrict__ scratch, size_t slot_bytes, int m_max) {
+            char* __restrict__ scratch, size_t slot_bytes, int m_max, int skip_s0) {
     constexpr int RD = R > 4 ? 4 : R;  // FP64 squaring tile
     constexpr size_t SMB = sizeof(GemmSmem<T, R>) > sizeof(GemmSmem<double, RD>) ? sizeof(GemmSmem<T, R>)
                                                                                    : sizeof(GemmSmem<double, RD>);
@@ -34,7 +34,7 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     __shared__ double s_if[32];   // 1/i!
     __shared__ double s_uk[8];
     __shared__ double s_scale;
-    __shared__ int s_sq, s_p, s_q;
+    __shared__ int s_sq, s_p, s_q, s_skip;
 
     // whole-problem launches walk the class's (block, slice) list; windowed launches (one problem,
     // checkpoint segments) index the window directly
@@ -93,7 +93,8 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
             s_p = c_deg_p[di];
             s_q = c_deg_q[di];
             s_scale = B.dt / (double)(1LL << s);
-            if (P.stats) {
+            s_skip = skip_s0 && s == 0;  // slices without squarings: the tensor-core kernel owns them
+            if (P.stats && !s_skip) {
                 const unsigned long long m3 = (unsigned long long)m * m * m;
                 atomicAdd(P.stats + 0, m3 * (unsigned long long)(c_deg_p[di] + c_deg_q[di] - 2));
                 atomicAdd(P.stats + 1, m3 * (unsigned long long)s);
@@ -101,6 +102,10 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
             }
         }
         __syncthreads();
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
         const int s = s_sq, p = s_p, q = s_q;
         const int d = p * q;
 
@@ -183,9 +188,9 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
 template <class T, int R>
 int launch_one(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
-               int grid, cudaStream_t st) {
+               int grid, int skip_s0, cudaStream_t st) {
     expm_kernel<T, R><<<grid, GEMM_THREADS, 0, st>>>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch,
-                                                     slot_bytes, m_max);
+                                                     slot_bytes, m_max, skip_s0);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
@@ -246,8 +251,9 @@ int expm_grid_limit(int prec, int R) {
 
 int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                 const int2* items, long long n_items, int R, void* Uout, char* scratch, size_t slot_bytes, int m_max,
-                int grid, cudaStream_t st) {
-#define QOC_L(TT, RR) launch_one<TT, RR>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes, m_max, grid, st)
+                int grid, cudaStream_t st, int skip_s0) {
+#define QOC_L(TT, RR) \
+    launch_one<TT, RR>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes, m_max, grid, skip_s0, st)
     if (P.prec == 0) {
         switch (R) {
             case 1: return QOC_L(double, 1);

@@ -1,10 +1,10 @@
 // Batched slice propagators on the tcgen05 tensor cores (Sec. II.A, Eq. exppropagator).
 //
 // U = exp(X)^(2^s), X = -i (tau / 2^s) H_k, for blocks of size m <= 112 in FP32 plans.  Every complex
-// product runs on the tensor cores through the FP16 hi/lo split of tc_gemm.cuh (three real products
-// per real product, FP32 accumulation in tensor memory), and the operands stay on chip from one
-// product to the next: the epilogue that drains an accumulator writes the next product's operands,
-// already split, straight into shared memory.
+// product runs on the tensor cores through the FP16 hi/lo split of tc_gemm.cuh (all four split
+// products per real product, small ones first, FP32 accumulation in tensor memory), and the operands
+// stay on chip from one product to the next: the epilogue that drains an accumulator writes the next
+// product's operands, already split, straight into shared memory.
 //
 // Polynomial.  The Taylor polynomial of odd degree 2q-1 is evaluated by Horner's rule in Y = X^2,
 //     T(X) = sum_{j<q} (c_{2j} I + c_{2j+1} X) Y^j,   c_k = 1/k!,
@@ -29,8 +29,9 @@
 // Scaling.  Each operand is scaled by a power of two 2^e before the split so that its entries stay
 // within 2^14 (the FP16 range is 65504): X by its norm bound beta, Y by beta^2, the Horner iterates by
 // e^beta, the squaring iterates by 2 (they are unitary up to rounding for Hermitian H).  An entry
-// outside the range latches ST_RANGE.  Two FP16 halves hold 22 significant bits, so a product's
-// rounding is about 2^-22 relative (FP32: 2^-24).
+// outside the range latches ST_RANGE.  Two FP16 halves hold 22 significant bits; with all four split
+// products and the small-first order a product's error is within about 2x that of an FP32 CUDA-core
+// product (the accumulator's own rounding is most of the rest).
 #include <cuda_fp16.h>
 
 #include "../../include/qoc.h"
@@ -110,16 +111,20 @@ __device__ __forceinline__ void ld_acc8(uint32_t t_re, uint32_t t_im, float (&re
 }
 
 // One thread: D(re at d_re, im at d_im) = A B for the complex operands whose plane groups start at
-// shared addresses a and b (A as rows, B as rows of B^T), three split products per real product.
+// shared addresses a and b (A as rows, B as rows of B^T), four split products per real product.
 __device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t plane, int NP, uint32_t d_re,
                                             uint32_t d_im) {
     const uint32_t lbo = 128, sbo = (uint32_t)(NP >> 3) * 128u;
     const uint32_t pos = idesc_f16(128, NP, false), neg = idesc_f16(128, NP, true);
-    const int ha[3] = {0, 0, 1}, hb[3] = {0, 1, 0};  // (hi,hi), (hi,lo), (lo,hi)
-    for (int kk = 0; kk < NP / 16; ++kk) {
-        const uint32_t step = (uint32_t)kk * 256u;
+    // (lo,lo), (hi,lo), (lo,hi) first, (hi,hi) last: the accumulator rounds each addition relative to
+    // its running magnitude, so the small terms are summed while it is still small and only the K/16
+    // large (hi,hi) additions meet a large accumulator.  Dropping lo*lo would bias products such as
+    // X X, whose lo parts are correlated.
+    const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};
 #pragma unroll
-        for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < 4; ++t) {
+        for (int kk = 0; kk < NP / 16; ++kk) {
+            const uint32_t step = (uint32_t)kk * 256u;
             const int acc = (kk > 0 || t > 0);
             const uint64_t ar = smem_desc_u32(a + ha[t] * plane + step, lbo, sbo);
             const uint64_t ai = smem_desc_u32(a + (2 + ha[t]) * plane + step, lbo, sbo);
@@ -169,13 +174,13 @@ __device__ __forceinline__ void xt_sync() {
 __global__ void __launch_bounds__(XT_THREADS, 1)
 expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int* __restrict__ cls_blocks, int n_cls,
                const int2* __restrict__ cls_items, long long n_cls_items, void* __restrict__ Uout,
-               char* __restrict__ scratch, size_t slot_bytes, int m_max, uint32_t tmem_cols) {
+               char* __restrict__ scratch, size_t slot_bytes, int m_max, uint32_t tmem_cols, int all_items) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ uint64_t bar;
     __shared__ uint32_t tslot;
     __shared__ float s_uf[8];
     __shared__ float s_c[36];  // 1/k!
-    __shared__ int s_q, s_s, s_eX, s_eY, s_eS;
+    __shared__ int s_q, s_s, s_eX, s_eY, s_eS, s_skip;
     __shared__ float s_sc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, half = warp >> 2;
@@ -252,8 +257,8 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             if (nan) atomicOr(P.status, ST_NAN_PULSE);
             beta *= B.dt;
             // Fewest squarings: each one doubles the error of what it squares, and a squaring here
-            // rounds at about 2^-22 (the split), so scaling further than the plan's largest
-            // norm loses more than the lower-degree polynomial gains.
+            // errs more than an FP32 one, so scaling further than the plan's largest norm loses
+            // more than the lower-degree polynomial gains.
             const double cap = tabs.theta_cap;
             int smin = 0;
             double b = beta;
@@ -265,13 +270,14 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             int bq = 1;
             while (bq < 16 && tabs.theta_odd[bq - 1] < ldexp(beta, -bs)) ++bq;
             const double bsn = ldexp(beta, -bs);
+            s_skip = !all_items && bs > 0;  // slices with squarings: the CUDA-core tiles own them
             s_q = bq;
             s_s = bs;
             s_sc = (float)ldexp(B.dt, -bs);
             s_eX = xt_exp_for(bsn);
             s_eY = xt_exp_for(bsn * bsn);
             s_eS = xt_exp_for(exp(bsn));
-            if (P.stats) {
+            if (P.stats && !s_skip) {
                 const unsigned long long m3 = (unsigned long long)m * m * m;
                 atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
                 atomicAdd(P.stats + 1, m3 * (unsigned long long)bs);
@@ -279,6 +285,10 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             }
         }
         __syncthreads();
+        if (s_skip) {
+            __syncthreads();
+            continue;
+        }
         const int q = s_q, s = s_s;
         const int eX = s_eX, eY = s_eY, eS = s_eS, eQ = 13;
         const bool sq64 = s > 0 && tabs.sq_f64;
@@ -576,13 +586,13 @@ int expm_tc_grid_limit(int m_max) {
 
 int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                    const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
-                   int grid, cudaStream_t st) {
+                   int grid, cudaStream_t st, int all_items) {
     if (m_max > XT_MAXM) return -1;
     const XtConfig c = xt_config(m_max);
     if (cudaFuncSetAttribute(expm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)c.smem) != cudaSuccess)
         return -1;
     expm_tc_kernel<<<grid, XT_THREADS, c.smem, st>>>(P, tabs, u, cls, n_cls, items, n_items, Uout, scratch, slot_bytes,
-                                                     m_max, c.tmem_cols);
+                                                     m_max, c.tmem_cols, all_items);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

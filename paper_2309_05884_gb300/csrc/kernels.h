@@ -24,9 +24,10 @@ int expm_r_for(int prec, int m);
 int expm_grid_limit(int prec, int R);
 // One launch per size class R: cls lists the class's blocks (windowed launches), items its
 // (block, slice) pairs (whole-problem launches, P.nk < 0).
+// skip_s0: leave the slices that need no squaring to the tensor-core kernel
 int launch_expm(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                 const int2* items, long long n_items, int R, void* Uout, char* scratch, size_t slot_bytes, int m_max,
-                int grid, cudaStream_t st);
+                int grid, cudaStream_t st, int skip_s0 = 0);
 // U_out[a_off[b] + k*m*m + e] (complex128, unpadded) <- the working-precision propagators.
 int launch_export_u(const DevPlan& P, const void* U, double2* U_out, const long long* a_off, cudaStream_t st);
 
@@ -46,9 +47,10 @@ int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, c
 int expm_tc_supported(int prec, int m);
 int expm_tc_grid_limit(int m_max);
 size_t expm_tc_slot_bytes(int m_max);
+// all_items: 1 = every slice on the tensor cores; 0 = only the slices that need no squaring
 int launch_expm_tc(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
                    const int2* items, long long n_items, void* Uout, char* scratch, size_t slot_bytes, int m_max,
-                   int grid, cudaStream_t st);
+                   int grid, cudaStream_t st, int all_items);
 
 // ---- sweep.cu
 // Forward (psi_{i+1} = U_i psi_i) and/or backward (lam_i = U_i^dagger lam_{i+1}) sweeps over the

@@ -27,6 +27,11 @@ struct ExpmClass {
     int m_max;
     int grid;
     size_t slot_bytes;
+    // tensor-core classes with R == 0 (slices without squarings only): the CUDA-core tile launch that
+    // takes the class's other slices
+    int R2 = 0;
+    int grid2 = 0;
+    size_t slot2 = 0;
 };
 
 // Kernel choice for blocks of size <= m_max (rules sorted by m_max; the first match wins).
@@ -185,9 +190,13 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
         if (c.kind == 1)
             rc = launch_expm_warp(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                   c.R, c.per_warp, ws + p->off_U, c.grid, st);
-        else if (c.kind == 2)
+        else if (c.kind == 2) {
             rc = launch_expm_tc(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
-                                ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st);
+                                ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st, c.R);
+            if (rc == 0 && c.R == 0)
+                rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                 c.R2, ws + p->off_U, ws + p->off_expm, c.slot2, c.m_max, c.grid2, st, 1);
+        }
         else
             rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items, c.R,
                              ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st);
@@ -272,7 +281,7 @@ int build_classes(qoc_plan* p) {
                 key = {1, MP, r.param > 0 ? std::min(r.param, 32 / MP) : 32 / MP};
             } else if (r.kind == 2) {
                 if (!expm_tc_supported(wp, m)) continue;
-                key = {2, 0, 0};
+                key = {2, r.param > 0 ? 1 : 0, 0};
             } else {
                 const int rmax = wp == QOC_PREC_F64 ? 4 : 7;
                 key = {0, r.param > 0 ? std::min(r.param, rmax) : expm_r_for(wp == QOC_PREC_F64 ? 0 : 1, m), 0};
@@ -312,6 +321,12 @@ int build_classes(qoc_plan* p) {
             c.grid = (int)std::max<long long>(1, std::min<long long>(max_items, expm_tc_grid_limit(c.m_max)));
             c.slot_bytes = align_up(expm_tc_slot_bytes(c.m_max), 256);
             p->expm_scratch = std::max(p->expm_scratch, c.slot_bytes * (size_t)c.grid);
+            if (c.R == 0) {  // the launches run in turn on one stream and share the scratch
+                c.R2 = expm_r_for(1, c.m_max);
+                c.grid2 = (int)std::max<long long>(1, std::min<long long>(max_items, expm_grid_limit(1, c.R2)));
+                c.slot2 = align_up(expm_slot_bytes(1, c.m_max), 256);
+                p->expm_scratch = std::max(p->expm_scratch, c.slot2 * (size_t)c.grid2);
+            }
         } else if (c.kind == 1) {
             const long long groups = (max_items + c.per_warp - 1) / c.per_warp;
             const long long ctas = (groups + (c.R == 32 ? 2 : 4) - 1) / (c.R == 32 ? 2 : 4);
@@ -591,8 +606,15 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     }
     p->tabs.sq_f64 = o.prec == QOC_PREC_F32_ALL ? 0 : 1;
 
-    // expm size classes (default rules: warp-packed kernel for the small blocks it supports)
-    p->rules.push_back({1 << 30, 0, 0});  // tiled kernels; the autotuner may pick the warp-packed one
+    // expm size classes.  In FP32 plans the slices of blocks with 25..112 states that need no
+    // squaring go to the tensor cores; a tensor-core product errs up to about 2x an FP32 one, so
+    // slices whose squarings would amplify that stay on the tiled CUDA-core kernels, as do all other
+    // blocks (the autotuner may pick the warp-packed or other tensor-core rules)
+    if (o.prec != QOC_PREC_F64) {
+        p->rules.push_back({24, 0, 0});
+        p->rules.push_back({112, 2, 0});
+    }
+    p->rules.push_back({1 << 30, 0, 0});
     {
         const int rc = build_classes(p);
         if (rc) {
@@ -761,7 +783,7 @@ int qoc_plan_work_counts(qoc_plan* p, long long* out, int n) {
     unsigned long long h[4] = {0, 0, 0, 0};
     cudaError_t e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats read");
-    for (int i = 0; i < n && i < 3; ++i) out[i] = (long long)h[i];
+    for (int i = 0; i < n && i < 4; ++i) out[i] = (long long)h[i];
     return QOC_OK;
 }
 
@@ -769,13 +791,15 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     if (!p || !launches) return set_error(QOC_EINVAL, "null argument");
     // gathers, one expm launch per size class, sweeps, overlap, slice derivatives, reduction
     // (+ the iteration counter when optimising); propagate: gather, expm, sweep, memset, store
-    const int ncls = (int)p->classes.size();
+    const int nrev = (int)p->classes.size();  // reverse-mode derivative launches: one per class
+    int ncls = 0;                               // exponential launches
+    for (const auto& c : p->classes) ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
     // register-tile derivative launches per gradient pass (FP32 plans): one per size range used
     const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? (p->max_m > 64 ? 2 : 1) : 0;
     if (p->nseg == 1)
-        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + ncls + 1 : 1 + ncls + 1 + 1;
+        *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + nrev + 1 : 1 + ncls + 1 + 1;
     else
-        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (2 * ncls + 2 + gfl) + 1
+        *launches = with_grad ? 1 + p->nseg * (ncls + 1) + 1 + 1 + p->nseg * (ncls + nrev + 2 + gfl) + 1
                               : 1 + p->nseg * (ncls + 1) + 1;
     return QOC_OK;
 }
@@ -806,6 +830,8 @@ int qoc_plan_set_expm_rules(qoc_plan* p, int n_rules, const int* m_max, const in
         if (kind[i] < 0 || kind[i] > 2)
             return set_error(QOC_EINVAL, "rule kind must be 0 (CTA tiles), 1 (warp-packed) or 2 (tensor cores)");
         if (param[i] < 0) return set_error(QOC_EINVAL, "rule parameter must be >= 0");
+        if (kind[i] == 2 && param[i] > 1)
+            return set_error(QOC_EINVAL, "tensor-core rule parameter must be 0 (unsquared slices) or 1 (all)");
         rules.push_back({m_max[i], kind[i], param[i]});
     }
     std::stable_sort(rules.begin(), rules.end(), [](const ExpmRule& a, const ExpmRule& b) { return a.m_max < b.m_max; });

@@ -1,14 +1,15 @@
 // Complex matrix products on the 5th-generation tensor cores, at about FP32 accuracy.
 //
 // C = A B for complex m x m matrices (m <= 112) given in FP32.  Each real part is split into two
-// FP16 numbers, x = hi + lo with hi = fp16(x) and lo = fp16(x - hi), and a product keeps
-// hi*hi + hi*lo + lo*hi (FP32 accumulation in tensor memory); the dropped lo*lo term and the FP16
-// rounding of lo are ~2^-22 relative to the operands.  The complex product is four real products
-// into two accumulators: C_r = A_r B_r - A_i B_i (the minus from the instruction's negate-A bit),
-// C_i = A_r B_i + A_i B_r.  One CTA of 128 threads owns a product: it stages both operands in shared
-// memory in the K-major no-swizzle canonical layout (8 x 16-byte core matrices), one thread issues
-// the tcgen05 MMAs (M = 128, N = m rounded up to 16, K = 16 per instruction), the commit arrives on
-// an mbarrier, and the four warps read the accumulators back row by row (warp w holds rows 32w..).
+// FP16 numbers, x = hi + lo with hi = fp16(x) and lo = fp16(x - hi), and a real product is the sum
+// of all four split products lo*lo, hi*lo, lo*hi, hi*hi, accumulated in FP32 in tensor memory in
+// that order (small terms first: each addition rounds relative to the running sum).  The complex
+// product is four real products into two accumulators: C_r = A_r B_r - A_i B_i (the minus from the
+// instruction's negate-A bit), C_i = A_r B_i + A_i B_r.  One CTA of 128 threads owns a product: it
+// stages both operands in shared memory in the K-major no-swizzle canonical layout (8 x 16-byte
+// core matrices), one thread issues the tcgen05 MMAs (M = 128, N = m rounded up to 16, K = 16 per
+// instruction), the commit arrives on an mbarrier, and the four warps read the accumulators back
+// row by row (warp w holds rows 32w..).
 #pragma once
 
 #include <cuda_fp16.h>
@@ -84,10 +85,12 @@ __device__ __forceinline__ void tc_issue(unsigned char* sm, const TcLayout& L, u
     const uint32_t lbo = 128, sbo = (uint32_t)(L.KP / 8) * 128;
     const uint32_t id_pos = idesc_f16(128, L.NP, false), id_neg = idesc_f16(128, L.NP, true);
     const uint32_t Cr = tmem, Ci = tmem + 128;
-    const int hiA[3] = {0, 0, 1}, hiB[3] = {0, 1, 0};  // (hi,hi), (hi,lo), (lo,hi)
-    for (int kk = 0; kk < L.KP / 16; ++kk) {
-        const size_t step = (size_t)kk * 256;  // two cores along K
-        for (int t = 0; t < 3; ++t) {
+    // (lo,lo), (hi,lo), (lo,hi) first and (hi,hi) last: the small terms are summed while the
+    // accumulator is small, so only the K/16 large additions round against a large running sum
+    const int hiA[4] = {1, 0, 1, 0}, hiB[4] = {1, 1, 0, 0};
+    for (int t = 0; t < 4; ++t) {
+        for (int kk = 0; kk < L.KP / 16; ++kk) {
+            const size_t step = (size_t)kk * 256;  // two cores along K
             const int first = (kk == 0 && t == 0);
             const uint64_t ar = smem_desc(sm + L.a_off(hiA[t]) + step, lbo, sbo);
             const uint64_t ai = smem_desc(sm + L.a_off(2 + hiA[t]) + step, lbo, sbo);

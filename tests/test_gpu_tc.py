@@ -72,6 +72,7 @@ def test_tensor_core_expm_matches_tiled_and_oracle(prec):
     plan = api.Plan(B, s.N, s.tau, prec=prec, active=B.active_copies(b0, bf))
     u = torch.from_numpy(I.pulses_normal(9, s.N, 3)).to(DEV)
     d0, df = api.to_device(b0, DEV), api.to_device(bf, DEV)
+    plan.set_expm_rules([(1 << 30, 0, 0)])
     o_t, g_t = plan.fidelity_and_grad(u, d0, df)
     plan.set_expm_rules([(112, 2, 0)])
     assert all(c[0] == 2 for c in plan.expm_classes())
@@ -87,17 +88,19 @@ def test_tensor_core_expm_matches_tiled_and_oracle(prec):
     assert np.linalg.norm(gc - g_t.cpu().numpy()) / np.linalg.norm(gref) <= 1e-5
 
 
-def _propagator_errors(system, prec, u, ckpt=0):
-    """Max |U - U_oracle| over every slice and block, for the tensor-core kernel and the tiled one.
-    The oracle exponentiates the basis builder's block Hamiltonians by eigendecomposition in FP64."""
+def _propagator_errors(system, prec, u, tc_param=1):
+    """Max |U - U_oracle| over every slice and block, for the tensor-core rule (tc_param 1: every
+    slice on the tensor cores; 0: the slices without squarings) and the tiled kernel.  The oracle
+    exponentiates the basis builder's block Hamiltonians by eigendecomposition in FP64."""
     from oracle import grape as gr
     from paper_2309_05884_gb300 import api
     B = api.Basis(system)
     plan = api.Plan(B, system.N, system.tau, prec=prec)
     ut = torch.from_numpy(np.ascontiguousarray(u)).to(DEV)
+    plan.set_expm_rules([(1 << 30, 0, 0)])
     U_t = plan.expm(ut).cpu().numpy()
-    plan.set_expm_rules([(112, 2, 0)])
-    assert all(c[0] == 2 for c in plan.expm_classes())
+    plan.set_expm_rules([(112, 2, tc_param)])
+    assert all(c[0] == 2 and c[1] == tc_param for c in plan.expm_classes())
     U_c = plan.expm(ut).cpu().numpy()
     torch.cuda.synchronize()
     plan.sync_status()
@@ -135,10 +138,20 @@ def test_tensor_core_propagators_match_oracle(case):
     u = I.pulses_normal(17, s.N, s.n_ctrl) if s.n_ctrl == 3 else I.pulses_uniform(17, s.N, s.n_ctrl)
     e_c, e_t = _propagator_errors(s, prec, u)
     assert e_c <= tol, (e_c, e_t)
-    # and within the split's precision of the FP32 CUDA-core kernel on the same slices: two FP16
-    # halves carry 22 significant bits against FP32's 24, and the dropped lo*lo term is of the same
-    # order, so up to about 8x its error
+    # and close to the FP32 CUDA-core kernel on the same slices (two FP16 halves per operand, all four
+    # split products: a product errs up to about 2x an FP32 one, more through many squarings)
     assert e_c <= max(8 * e_t, tol / 4), (e_c, e_t)
+
+
+@pytest.mark.parametrize("prec", ["f32", "f32_all"])
+def test_tensor_core_rule_keeps_squared_slices_on_cuda_cores(prec):
+    # |tau H| ~ 50: every slice needs squarings, so the default tensor-core rule (param 0) leaves them
+    # all to the tiled kernel and the result has its accuracy
+    from paper_2309_05884_gb300 import inputs as I
+    s = I.xxz_ring(8, 20.0, 5)
+    u = I.pulses_normal(17, s.N, 3)
+    e_c, e_t = _propagator_errors(s, prec, u, tc_param=0)
+    assert e_c <= 1.0001 * e_t + 1e-12, (e_c, e_t)
 
 
 def test_tensor_core_expm_in_checkpoint_windows():
