@@ -103,4 +103,55 @@ struct DevPlan {
     unsigned long long* stats; // work counters or null
 };
 
+// Norm bound of slice k (0-based) of block B: beta = tau (|H0|_1 + sum_j |u_kj| |Hc_j|_1), the 1-norm
+// bound that fixes the squarings of the exponential and the series lengths (Sec. II.A).  Non-finite
+// pulse values count as 0 (the kernels latch ST_NAN_PULSE).  Every kernel that decides which
+// slices it owns uses this function, so that the decisions of different kernels agree exactly.
+__device__ __forceinline__ double slice_beta(const DevPlan& P, const DevBlock& B, const double* u, long long k) {
+    double beta = B.h0_norm1;
+    for (int j = 0; j < P.nc; ++j) {
+        const double x = u[(size_t)(B.u_row + k) * P.nc + j];
+        beta += fabs(isfinite(x) ? x : 0.0) * B.hc_norm1[j];
+    }
+    return beta * B.dt;
+}
+
+// Halvings s that bring beta under cap, at most max_s; *scaled (may be null) receives beta / 2^s.
+__device__ __forceinline__ int slice_halvings(double beta, double cap, int max_s, double* scaled = nullptr) {
+    int s = 0;
+    while (beta > cap && s < max_s) {
+        beta *= 0.5;
+        ++s;
+    }
+    if (scaled) *scaled = beta;
+    return s;
+}
+
+// The items blockIdx.x + i * gridDim.x (i = 0, 1, ...) of a grid-stride loop over [0, total), tested
+// blockDim.x at a time in parallel: want(item) decides on one thread, the kept ones are listed in
+// increasing order in list (capacity blockDim.x) and counted in *n (wcnt: 32 ints of scratch).
+// Returns false once the CTA has no items left.  Call from every thread; the caller walks
+// list[0 .. *n) and then calls again with base += blockDim.x.
+template <class Want>
+__device__ __forceinline__ bool cta_select(long long total, long long base, Want want, int* list, int* n, int* wcnt) {
+    if ((long long)blockIdx.x + base * gridDim.x >= total) return false;
+    __syncthreads();  // every thread is done with the previous list
+    const long long item = (long long)blockIdx.x + (base + threadIdx.x) * gridDim.x;
+    const bool keep = item < total && want(item);
+    const unsigned bal = __ballot_sync(0xffffffffu, keep);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) wcnt[warp] = __popc(bal);
+    __syncthreads();
+    int off = 0;
+    for (int w = 0; w < warp; ++w) off += wcnt[w];
+    if (keep) list[off + __popc(bal & ((1u << lane) - 1u))] = (int)threadIdx.x;
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += wcnt[w];
+        *n = t;
+    }
+    __syncthreads();
+    return true;
+}
+
 }  // namespace qoc

@@ -34,7 +34,7 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     __shared__ double s_if[32];   // 1/i!
     __shared__ double s_uk[8];
     __shared__ double s_scale;
-    __shared__ int s_sq, s_p, s_q, s_skip;
+    __shared__ int s_sq, s_p, s_q;
 
     // whole-problem launches walk the class's (block, slice) list; windowed launches (one problem,
     // checkpoint segments) index the window directly
@@ -56,132 +56,149 @@ expm_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const int*
     }
     if (threadIdx.x < 8) pw[threadIdx.x] = base + (size_t)(threadIdx.x < 6 ? threadIdx.x : 0) * mm_max;
 
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        int bi, kw, k;  // block, slot in the window, slice (0-based)
+    __shared__ int s_list[GEMM_THREADS];
+    __shared__ int s_nl;
+    __shared__ int s_wc[32];
+    // slices this launch owns: all of them, or (skip_s0) those that need squarings
+    auto want = [&](long long it) -> bool {
+        if (!skip_s0) return true;
+        int bi;
+        long long k;
         if (whole) {
-            const int2 it = cls_items[item];
-            bi = it.x;
-            kw = it.y;
-            k = it.y;
+            const int2 e = cls_items[it];
+            bi = e.x;
+            k = e.y;
         } else {
-            bi = cls_blocks[item / NK];
-            kw = (int)(item % NK);
-            k = P.k0 + kw;
+            bi = cls_blocks[it / NK];
+            k = P.k0 + it % NK;
         }
-        const DevBlock& B = P.blocks[bi];
-        const int m = B.m;
-        const size_t mm = (size_t)m * m;
-
-        if (threadIdx.x == 0) {
-            double beta = B.h0_norm1;
-            int bad = 0;
-            for (int j = 0; j < P.nc; ++j) {
-                const double uk = u[(size_t)(B.u_row + k) * P.nc + j];
-                const int fin = isfinite(uk);
-                bad |= !fin;
-                s_uk[j] = fin ? uk : 0.0;
-                beta += fabs(s_uk[j]) * B.hc_norm1[j];
+        return slice_halvings(slice_beta(P, P.blocks[bi], u, k), tabs.theta_cap, P.max_sq) > 0;
+    };
+    for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
+        const int nl = s_nl;
+        for (int li = 0; li < nl; ++li) {
+            const long long item = (long long)blockIdx.x + (lb + s_list[li]) * gridDim.x;
+            int bi, kw, k;  // block, slot in the window, slice (0-based)
+            if (whole) {
+                const int2 it = cls_items[item];
+                bi = it.x;
+                kw = it.y;
+                k = it.y;
+            } else {
+                bi = cls_blocks[item / NK];
+                kw = (int)(item % NK);
+                k = P.k0 + kw;
             }
-            if (bad) atomicOr(P.status, ST_NAN_PULSE);
-            beta *= B.dt;
-            int s = 0;
-            while (beta > tabs.theta_cap && s < P.max_sq) { beta *= 0.5; ++s; }
-            if (beta > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
-            int di = 0;
-            while (di < tabs.n_deg - 1 && tabs.theta[di] < beta) ++di;
-            s_sq = s;
-            s_p = c_deg_p[di];
-            s_q = c_deg_q[di];
-            s_scale = B.dt / (double)(1LL << s);
-            s_skip = skip_s0 && s == 0;  // slices without squarings: the tensor-core kernel owns them
-            if (P.stats && !s_skip) {
-                const unsigned long long m3 = (unsigned long long)m * m * m;
-                atomicAdd(P.stats + 0, m3 * (unsigned long long)(c_deg_p[di] + c_deg_q[di] - 2));
-                atomicAdd(P.stats + 1, m3 * (unsigned long long)s);
-                atomicAdd(P.stats + 2, 1ull);
-            }
-        }
-        __syncthreads();
-        if (s_skip) {
-            __syncthreads();
-            continue;
-        }
-        const int s = s_sq, p = s_p, q = s_q;
-        const int d = p * q;
+            const DevBlock& B = P.blocks[bi];
+            const int m = B.m;
+            const size_t mm = (size_t)m * m;
 
-        // X = -i (tau / 2^s) (H0 + sum_j u_j Hc_j)
-        {
-            const cx<T>* H = reinterpret_cast<const cx<T>*>(P.H) + B.h_off;
-            const T sc = (T)s_scale;
-            cx<T>* X = base + mm_max;
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                cx<T> h = H[e];
+            if (threadIdx.x == 0) {
+                double beta = B.h0_norm1;
+                int bad = 0;
                 for (int j = 0; j < P.nc; ++j) {
-                    const cx<T> hc = H[(size_t)(1 + j) * mm + e];
-                    const T uj = (T)s_uk[j];
-                    h.x = fma(uj, hc.x, h.x);
-                    h.y = fma(uj, hc.y, h.y);
+                    const double uk = u[(size_t)(B.u_row + k) * P.nc + j];
+                    const int fin = isfinite(uk);
+                    bad |= !fin;
+                    s_uk[j] = fin ? uk : 0.0;
+                    beta += fabs(s_uk[j]) * B.hc_norm1[j];
                 }
-                X[e] = cmul_mis<T>(h, sc);
-            }
-        }
-        __syncthreads();
-        // X^2 .. X^p
-        for (int i = 2; i <= p; ++i)
-            cta_gemm<T, R>(base + i * mm_max, base + (i - 1) * mm_max, base + mm_max, m, 0, nullptr, nullptr, sm);
-
-        // Paterson-Stockmeyer: S = c_d X^p + sum_{l<p} c_{(q-1)p+l} X^l, then
-        // S <- S X^p + sum_{l<p} c_{kb p + l} X^l for kb = q-2 .. 0  (c_i = 1/i!)
-        cx<T>* S = S0;
-        cx<T>* Sn = S1;
-        {
-            const T cd = (T)s_if[d];
-            const cx<T>* Xpp = base + p * mm_max;
-            const int b0 = (q - 1) * p;
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                const int row = (int)(e / m), col = (int)(e - (size_t)row * m);
-                cx<T> v = cscale<T>(Xpp[e], cd);
-                if (row == col) v.x += (T)s_if[b0];
-                for (int l = 1; l < p; ++l) {
-                    const cx<T> xv = pw[l][e];
-                    const T c = (T)s_if[b0 + l];
-                    v.x = fma(c, xv.x, v.x);
-                    v.y = fma(c, xv.y, v.y);
+                if (bad) atomicOr(P.status, ST_NAN_PULSE);
+                beta *= B.dt;
+                int s = 0;
+                while (beta > tabs.theta_cap && s < P.max_sq) { beta *= 0.5; ++s; }
+                if (beta > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
+                int di = 0;
+                while (di < tabs.n_deg - 1 && tabs.theta[di] < beta) ++di;
+                s_sq = s;
+                s_p = c_deg_p[di];
+                s_q = c_deg_q[di];
+                s_scale = B.dt / (double)(1LL << s);
+                if (P.stats) {
+                    const unsigned long long m3 = (unsigned long long)m * m * m;
+                    atomicAdd(P.stats + 0, m3 * (unsigned long long)(c_deg_p[di] + c_deg_q[di] - 2));
+                    atomicAdd(P.stats + 1, m3 * (unsigned long long)s);
+                    atomicAdd(P.stats + 2, 1ull);
                 }
-                S[e] = v;
             }
-        }
-        __syncthreads();
-        for (int kb = q - 2; kb >= 0; --kb) {
-            if (threadIdx.x < p) coef[threadIdx.x] = (T)s_if[kb * p + threadIdx.x];
             __syncthreads();
-            cta_gemm<T, R>(Sn, S, base + p * mm_max, m, p, coef, pw, sm);
-            cx<T>* t = S; S = Sn; Sn = t;
-        }
+            const int s = s_sq, p = s_p, q = s_q;
+            const int d = p * q;
 
-        // s squarings in FP64, then store in the working precision
-        cx<T>* Uo = reinterpret_cast<cx<T>*>(Uout) + B.u_off + (size_t)kw * B.mmp;
-        if (s == 0) {
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
-        } else if (!tabs.sq_f64 && sizeof(T) == sizeof(float)) {
-            // squaring chain in the working precision
-            for (int i = 0; i < s; ++i) {
-                cta_gemm<T, R>(Sn, S, S, m, 0, nullptr, nullptr, sm);
+            // X = -i (tau / 2^s) (H0 + sum_j u_j Hc_j)
+            {
+                const cx<T>* H = reinterpret_cast<const cx<T>*>(P.H) + B.h_off;
+                const T sc = (T)s_scale;
+                cx<T>* X = base + mm_max;
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                    cx<T> h = H[e];
+                    for (int j = 0; j < P.nc; ++j) {
+                        const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                        const T uj = (T)s_uk[j];
+                        h.x = fma(uj, hc.x, h.x);
+                        h.y = fma(uj, hc.y, h.y);
+                    }
+                    X[e] = cmul_mis<T>(h, sc);
+                }
+            }
+            __syncthreads();
+            // X^2 .. X^p
+            for (int i = 2; i <= p; ++i)
+                cta_gemm<T, R>(base + i * mm_max, base + (i - 1) * mm_max, base + mm_max, m, 0, nullptr, nullptr, sm);
+
+            // Paterson-Stockmeyer: S = c_d X^p + sum_{l<p} c_{(q-1)p+l} X^l, then
+            // S <- S X^p + sum_{l<p} c_{kb p + l} X^l for kb = q-2 .. 0  (c_i = 1/i!)
+            cx<T>* S = S0;
+            cx<T>* Sn = S1;
+            {
+                const T cd = (T)s_if[d];
+                const cx<T>* Xpp = base + p * mm_max;
+                const int b0 = (q - 1) * p;
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                    const int row = (int)(e / m), col = (int)(e - (size_t)row * m);
+                    cx<T> v = cscale<T>(Xpp[e], cd);
+                    if (row == col) v.x += (T)s_if[b0];
+                    for (int l = 1; l < p; ++l) {
+                        const cx<T> xv = pw[l][e];
+                        const T c = (T)s_if[b0 + l];
+                        v.x = fma(c, xv.x, v.x);
+                        v.y = fma(c, xv.y, v.y);
+                    }
+                    S[e] = v;
+                }
+            }
+            __syncthreads();
+            for (int kb = q - 2; kb >= 0; --kb) {
+                if (threadIdx.x < p) coef[threadIdx.x] = (T)s_if[kb * p + threadIdx.x];
+                __syncthreads();
+                cta_gemm<T, R>(Sn, S, base + p * mm_max, m, p, coef, pw, sm);
                 cx<T>* t = S; S = Sn; Sn = t;
             }
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
-        } else {
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) D0[e] = ccast<double, T>(S[e]);
-            __syncthreads();
-            double2* Da = D0;
-            double2* Db = D1;
-            for (int i = 0; i < s; ++i) {
-                cta_gemm<double, RD>(Db, Da, Da, m, 0, nullptr, nullptr, smd);
-                double2* t = Da; Da = Db; Db = t;
+
+            // s squarings in FP64, then store in the working precision
+            cx<T>* Uo = reinterpret_cast<cx<T>*>(Uout) + B.u_off + (size_t)kw * B.mmp;
+            if (s == 0) {
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
+            } else if (!tabs.sq_f64 && sizeof(T) == sizeof(float)) {
+                // squaring chain in the working precision
+                for (int i = 0; i < s; ++i) {
+                    cta_gemm<T, R>(Sn, S, S, m, 0, nullptr, nullptr, sm);
+                    cx<T>* t = S; S = Sn; Sn = t;
+                }
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = S[e];
+            } else {
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) D0[e] = ccast<double, T>(S[e]);
+                __syncthreads();
+                double2* Da = D0;
+                double2* Db = D1;
+                for (int i = 0; i < s; ++i) {
+                    cta_gemm<double, RD>(Db, Da, Da, m, 0, nullptr, nullptr, smd);
+                    double2* t = Da; Da = Db; Db = t;
+                }
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = ccast<T, double>(Da[e]);
             }
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = ccast<T, double>(Da[e]);
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 

@@ -180,7 +180,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
     __shared__ uint32_t tslot;
     __shared__ float s_uf[8];
     __shared__ float s_c[36];  // 1/k!
-    __shared__ int s_q, s_s, s_eX, s_eY, s_eS, s_skip;
+    __shared__ int s_q, s_s, s_eX, s_eY, s_eS;
     __shared__ float s_sc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int quarter = warp & 3, half = warp >> 2;
@@ -226,305 +226,322 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
 
     const bool whole = P.nk < 0;
     const long long total = whole ? n_cls_items : (long long)n_cls * P.nk;
-    for (long long item = blockIdx.x; item < total && !failed; item += gridDim.x) {
-        int bi, kw, k;
+    __shared__ int s_list[XT_THREADS];
+    __shared__ int s_nl;
+    __shared__ int s_wc[32];
+    // slices this launch owns: all of them, or those that need no squaring
+    auto want = [&](long long it) -> bool {
+        if (all_items) return true;
+        int bi;
+        long long k;
         if (whole) {
-            const int2 it = cls_items[item];
-            bi = it.x;
-            kw = it.y;
-            k = it.y;
+            const int2 e = cls_items[it];
+            bi = e.x;
+            k = e.y;
         } else {
-            bi = cls_blocks[item / P.nk];
-            kw = (int)(item % P.nk);
-            k = P.k0 + kw;
+            bi = cls_blocks[it / P.nk];
+            k = P.k0 + it % P.nk;
         }
-        const DevBlock& B = P.blocks[bi];
-        const int m = B.m, NP = xt_pad16(m), nkg = NP / 8;
-        const size_t mm = (size_t)m * m;
-        const uint32_t plane = (uint32_t)NP * NP * 2u;
-        const uint32_t oBT = 0, oA = 4 * plane;  // plane groups (byte offsets)
-        const uint32_t aBT = sm_base + oBT, aA = sm_base + oA;
-        if (threadIdx.x == 0) {
-            double beta = B.h0_norm1;
-            int nan = 0;
-            for (int j = 0; j < P.nc; ++j) {
-                const double x = u[(size_t)(B.u_row + k) * P.nc + j];
-                const int fin = isfinite(x);
-                nan |= !fin;
-                s_uf[j] = fin ? (float)x : 0.f;
-                beta += fabs(fin ? x : 0.0) * B.hc_norm1[j];
+        return slice_halvings(slice_beta(P, P.blocks[bi], u, k), tabs.theta_cap, P.max_sq) == 0;
+    };
+    for (long long lb = 0; !failed && cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
+        const int nl = s_nl;
+        for (int li = 0; li < nl && !failed; ++li) {
+            const long long item = (long long)blockIdx.x + (lb + s_list[li]) * gridDim.x;
+            int bi, kw, k;
+            if (whole) {
+                const int2 it = cls_items[item];
+                bi = it.x;
+                kw = it.y;
+                k = it.y;
+            } else {
+                bi = cls_blocks[item / P.nk];
+                kw = (int)(item % P.nk);
+                k = P.k0 + kw;
             }
-            if (nan) atomicOr(P.status, ST_NAN_PULSE);
-            beta *= B.dt;
-            // Fewest squarings: each one doubles the error of what it squares, and a squaring here
-            // errs more than an FP32 one, so scaling further than the plan's largest norm loses
-            // more than the lower-degree polynomial gains.
-            const double cap = tabs.theta_cap;
-            int smin = 0;
-            double b = beta;
-            while (b > cap && smin < P.max_sq) { b *= 0.5; ++smin; }
-            if (b > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
-            // fewest squarings (each one doubles the rounding error of the polynomial), then the
-            // lowest odd degree whose truncation bound covers the scaled norm
-            const int bs = smin;
-            int bq = 1;
-            while (bq < 16 && tabs.theta_odd[bq - 1] < ldexp(beta, -bs)) ++bq;
-            const double bsn = ldexp(beta, -bs);
-            s_skip = !all_items && bs > 0;  // slices with squarings: the CUDA-core tiles own them
-            s_q = bq;
-            s_s = bs;
-            s_sc = (float)ldexp(B.dt, -bs);
-            s_eX = xt_exp_for(bsn);
-            s_eY = xt_exp_for(bsn * bsn);
-            s_eS = xt_exp_for(exp(bsn));
-            if (P.stats && !s_skip) {
-                const unsigned long long m3 = (unsigned long long)m * m * m;
-                atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
-                atomicAdd(P.stats + 1, m3 * (unsigned long long)bs);
-                atomicAdd(P.stats + 2, 1ull);
-            }
-        }
-        __syncthreads();
-        if (s_skip) {
-            __syncthreads();
-            continue;
-        }
-        const int q = s_q, s = s_s;
-        const int eX = s_eX, eY = s_eY, eS = s_eS, eQ = 13;
-        const bool sq64 = s > 0 && tabs.sq_f64;
-        float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
-
-        // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1 (one read of H)
-        {
-            const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
-            const float sc = s_sc, sig = ldexpf(1.f, eX);
-            const bool rin = r < m;
-            for (int g = half; g < nkg; g += 2) {
-                float2 h[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    const int col = 8 * g + c;
-                    h[c] = (rin && col < m) ? H[(size_t)r * m + col] : make_float2(0.f, 0.f);
+            const DevBlock& B = P.blocks[bi];
+            const int m = B.m, NP = xt_pad16(m), nkg = NP / 8;
+            const size_t mm = (size_t)m * m;
+            const uint32_t plane = (uint32_t)NP * NP * 2u;
+            const uint32_t oBT = 0, oA = 4 * plane;  // plane groups (byte offsets)
+            const uint32_t aBT = sm_base + oBT, aA = sm_base + oA;
+            if (threadIdx.x == 0) {
+                double beta = B.h0_norm1;
+                int nan = 0;
+                for (int j = 0; j < P.nc; ++j) {
+                    const double x = u[(size_t)(B.u_row + k) * P.nc + j];
+                    const int fin = isfinite(x);
+                    nan |= !fin;
+                    s_uf[j] = fin ? (float)x : 0.f;
+                    beta += fabs(fin ? x : 0.0) * B.hc_norm1[j];
                 }
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {  // every load of a matrix's 8 entries in flight together
-                    if (j < P.nc) {
-                        const float2* Hj = H + (size_t)(1 + j) * mm + (size_t)r * m;
-                        const float uj = s_uf[j];
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            const int col = 8 * g + c;
-                            if (rin && col < m) {
-                                const float2 hc = Hj[col];
-                                h[c].x = fmaf(uj, hc.x, h[c].x);
-                                h[c].y = fmaf(uj, hc.y, h[c].y);
+                if (nan) atomicOr(P.status, ST_NAN_PULSE);
+                beta *= B.dt;
+                // Fewest squarings: each one doubles the error of what it squares, and a squaring here
+                // errs more than an FP32 one, so scaling further than the plan's largest norm loses
+                // more than the lower-degree polynomial gains.
+                const double cap = tabs.theta_cap;
+                int smin = 0;
+                double b = beta;
+                while (b > cap && smin < P.max_sq) { b *= 0.5; ++smin; }
+                if (b > tabs.theta_cap) atomicOr(P.status, ST_SQUARING_CAP);
+                // fewest squarings (each one doubles the rounding error of the polynomial), then the
+                // lowest odd degree whose truncation bound covers the scaled norm
+                const int bs = smin;
+                int bq = 1;
+                while (bq < 16 && tabs.theta_odd[bq - 1] < ldexp(beta, -bs)) ++bq;
+                const double bsn = ldexp(beta, -bs);
+                s_q = bq;
+                s_s = bs;
+                s_sc = (float)ldexp(B.dt, -bs);
+                s_eX = xt_exp_for(bsn);
+                s_eY = xt_exp_for(bsn * bsn);
+                s_eS = xt_exp_for(exp(bsn));
+                if (P.stats) {
+                    const unsigned long long m3 = (unsigned long long)m * m * m;
+                    atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
+                    atomicAdd(P.stats + 1, m3 * (unsigned long long)bs);
+                    atomicAdd(P.stats + 2, 1ull);
+                }
+            }
+            __syncthreads();
+            const int q = s_q, s = s_s;
+            const int eX = s_eX, eY = s_eY, eS = s_eS, eQ = 13;
+            const bool sq64 = s > 0 && tabs.sq_f64;
+            float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
+
+            // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1 (one read of H)
+            {
+                const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
+                const float sc = s_sc, sig = ldexpf(1.f, eX);
+                const bool rin = r < m;
+                for (int g = half; g < nkg; g += 2) {
+                    float2 h[8];
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const int col = 8 * g + c;
+                        h[c] = (rin && col < m) ? H[(size_t)r * m + col] : make_float2(0.f, 0.f);
+                    }
+    #pragma unroll
+                    for (int j = 0; j < 8; ++j) {  // every load of a matrix's 8 entries in flight together
+                        if (j < P.nc) {
+                            const float2* Hj = H + (size_t)(1 + j) * mm + (size_t)r * m;
+                            const float uj = s_uf[j];
+    #pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                const int col = 8 * g + c;
+                                if (rin && col < m) {
+                                    const float2 hc = Hj[col];
+                                    h[c].x = fmaf(uj, hc.x, h[c].x);
+                                    h[c].y = fmaf(uj, hc.y, h[c].y);
+                                }
                             }
                         }
                     }
-                }
-                float xr[8], xi[8];
-#pragma unroll
-                for (int c = 0; c < 8; ++c) {
-                    xr[c] = h[c].y * sc;
-                    xi[c] = -h[c].x * sc;
-                }
-                if (r < NP) {
-                    put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
-                    if (q >= 2) put_ident8(sm, oBT, NP, r, g);  // for the transpose below
-                }
-                tmem_st8(R1re + 8 * g, xr);
-                tmem_st8(R1im + 8 * g, xi);
-            }
-            tmem_wait_st();
-            xt_sync();
-        }
-        // X^T (rows into the B^T planes), needed by the Horner steps: the product I X on the tensor
-        // cores, exactly the split sum of each entry, replaces a second, transposed read of H
-        if (q >= 2) {
-            if (threadIdx.x == 0) {
-                tc_fence_after();
-                issue_ident(aBT, aA, plane, NP, T0re, T0im);
-                mma_commit(&bar);
-            }
-            if (!mma_wait()) { failed = true; break; }
-            for (int g = half; g < nkg; g += 2) {
-                float dr[8], di[8];
-                ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-                if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
-            }
-            xt_sync();
-        }
-
-        // last polynomial value of row r, columns 8g..: to U, to the FP64 chain, or into the operands
-        // of the first squaring (A planes, and the identity into the first B^T plane)
-        auto finish8 = [&](int g, const float (&vr)[8], const float (&vi)[8]) {
-            if (s == 0) {
-                if (r < m) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(vr[c], vi[c]);
-                }
-            } else if (sq64) {
-                if (r < m) {
-#pragma unroll
-                    for (int c = 0; c < 8; ++c)
-                        if (8 * g + c < m) D0[(size_t)r * m + 8 * g + c] = make_double2(vr[c], vi[c]);
-                }
-            } else if (r < NP) {
-                put8(sm, oA, plane, NP, r, g, vr, vi, ldexpf(1.f, eQ), bad);
-                put_ident8(sm, oBT, NP, r, g);
-            }
-        };
-
-        // ---- polynomial: Y^T = X^T X^T, then Horner in Y
-        if (q >= 2) {
-            if (threadIdx.x == 0) {
-                tc_fence_after();
-                issue_cprod(aBT, aA, plane, NP, T0re, T0im);
-                mma_commit(&bar);
-            }
-            if (!mma_wait()) { failed = true; break; }
-            {
-                const float fY = ldexpf(1.f, -2 * eX), sigY = ldexpf(1.f, eY), sigS = ldexpf(1.f, eS);
-                const float c1 = s_c[2 * q - 1], c0 = s_c[2 * q - 2];
-                for (int g = half; g < nkg; g += 2) {
-                    float dr[8], di[8], xr[8], xi[8];
-                    ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-                    ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
-                    if (r < NP) {
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            dr[c] *= fY;
-                            di[c] *= fY;
-                        }
-                        put8(sm, oBT, plane, NP, r, g, dr, di, sigY, bad);
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            dr[c] = c1 * xr[c] + ((8 * g + c == r && r < m) ? c0 : 0.f);
-                            di[c] = c1 * xi[c];
-                        }
-                        put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
-                    }
-                }
-                xt_sync();
-            }
-            for (int j = q - 2; j >= 0 && !failed; --j) {
-                if (threadIdx.x == 0) {
-                    tc_fence_after();
-                    issue_cprod(aA, aBT, plane, NP, T0re, T0im);
-                    mma_commit(&bar);
-                }
-                if (!mma_wait()) { failed = true; break; }
-                const float f = ldexpf(1.f, -(eS + eY)), sigS = ldexpf(1.f, eS);
-                const float c1 = s_c[2 * j + 1], c0 = s_c[2 * j];
-                for (int g = half; g < nkg; g += 2) {
-                    float dr[8], di[8], xr[8], xi[8];
-                    ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-                    ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
-#pragma unroll
+                    float xr[8], xi[8];
+    #pragma unroll
                     for (int c = 0; c < 8; ++c) {
-                        dr[c] = fmaf(dr[c], f, c1 * xr[c]) + ((8 * g + c == r && r < m) ? c0 : 0.f);
-                        di[c] = fmaf(di[c], f, c1 * xi[c]);
+                        xr[c] = h[c].y * sc;
+                        xi[c] = -h[c].x * sc;
                     }
-                    if (j > 0) {
-                        if (r < NP) put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
-                    } else {
-                        finish8(g, dr, di);
+                    if (r < NP) {
+                        put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
+                        if (q >= 2) put_ident8(sm, oBT, NP, r, g);  // for the transpose below
                     }
+                    tmem_st8(R1re + 8 * g, xr);
+                    tmem_st8(R1im + 8 * g, xi);
                 }
+                tmem_wait_st();
                 xt_sync();
             }
-            if (failed) break;
-        } else {
-            // degree 1: T(X) = I + X
-            for (int g = half; g < nkg; g += 2) {
-                float xr[8], xi[8];
-                ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
-#pragma unroll
-                for (int c = 0; c < 8; ++c) xr[c] += (8 * g + c == r && r < m) ? 1.f : 0.f;
-                finish8(g, xr, xi);
-            }
-            xt_sync();
-        }
-
-        // ---- squarings
-        if (s > 0 && !sq64) {
-            // S^T from the product with the identity, into the B^T planes (scale carried over)
-            if (threadIdx.x == 0) {
-                tc_fence_after();
-                issue_ident(aBT, aA, plane, NP, T1re, T1im);
-                mma_commit(&bar);
-            }
-            if (!mma_wait()) { failed = true; break; }
-            for (int g = half; g < nkg; g += 2) {
-                float dr[8], di[8];
-                ld_acc8(R1re + 8 * g, R1im + 8 * g, dr, di);
-                if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
-            }
-            xt_sync();
-            const float f = ldexpf(1.f, -2 * eQ), sigQ = ldexpf(1.f, eQ);
-            for (int i = 1; i <= s && !failed; ++i) {
-                const bool last = i == s;
+            // X^T (rows into the B^T planes), needed by the Horner steps: the product I X on the tensor
+            // cores, exactly the split sum of each entry, replaces a second, transposed read of H
+            if (q >= 2) {
                 if (threadIdx.x == 0) {
                     tc_fence_after();
-                    issue_cprod(aA, aBT, plane, NP, T0re, T0im);                // S^2
-                    if (!last) issue_cprod(aBT, aA, plane, NP, T1re, T1im);    // (S^2)^T
+                    issue_ident(aBT, aA, plane, NP, T0re, T0im);
                     mma_commit(&bar);
                 }
                 if (!mma_wait()) { failed = true; break; }
                 for (int g = half; g < nkg; g += 2) {
                     float dr[8], di[8];
                     ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        dr[c] *= f;
-                        di[c] *= f;
-                    }
-                    if (last) {
-                        if (r < m) {
-#pragma unroll
-                            for (int c = 0; c < 8; ++c)
-                                if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(dr[c], di[c]);
-                        }
-                    } else {
-                        float tr[8], ti[8];
-                        ld_acc8(R1re + 8 * g, R1im + 8 * g, tr, ti);
-                        if (r < NP) {
-                            put8(sm, oA, plane, NP, r, g, dr, di, sigQ, bad);
-#pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                tr[c] *= f;
-                                ti[c] *= f;
-                            }
-                            put8(sm, oBT, plane, NP, r, g, tr, ti, sigQ, bad);
-                        }
-                    }
+                    if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
                 }
                 xt_sync();
             }
-            if (failed) break;
-        } else if (sq64) {
-            // FP64 squaring chain on the CUDA cores
-            double2* Da = D0;
-            double2* Db = D1;
-            for (int i = 0; i < s; ++i) {
-                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                    const int row = (int)(e / m), col = (int)(e - (size_t)row * m);
-                    double2 acc = make_double2(0.0, 0.0);
-                    for (int kk = 0; kk < m; ++kk) {
-                        const double2 a = Da[(size_t)row * m + kk], b = Da[(size_t)kk * m + col];
-                        acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
-                        acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+
+            // last polynomial value of row r, columns 8g..: to U, to the FP64 chain, or into the operands
+            // of the first squaring (A planes, and the identity into the first B^T plane)
+            auto finish8 = [&](int g, const float (&vr)[8], const float (&vi)[8]) {
+                if (s == 0) {
+                    if (r < m) {
+    #pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(vr[c], vi[c]);
                     }
-                    Db[e] = acc;
+                } else if (sq64) {
+                    if (r < m) {
+    #pragma unroll
+                        for (int c = 0; c < 8; ++c)
+                            if (8 * g + c < m) D0[(size_t)r * m + 8 * g + c] = make_double2(vr[c], vi[c]);
+                    }
+                } else if (r < NP) {
+                    put8(sm, oA, plane, NP, r, g, vr, vi, ldexpf(1.f, eQ), bad);
+                    put_ident8(sm, oBT, NP, r, g);
                 }
-                __syncthreads();
-                double2* t = Da;
-                Da = Db;
-                Db = t;
+            };
+
+            // ---- polynomial: Y^T = X^T X^T, then Horner in Y
+            if (q >= 2) {
+                if (threadIdx.x == 0) {
+                    tc_fence_after();
+                    issue_cprod(aBT, aA, plane, NP, T0re, T0im);
+                    mma_commit(&bar);
+                }
+                if (!mma_wait()) { failed = true; break; }
+                {
+                    const float fY = ldexpf(1.f, -2 * eX), sigY = ldexpf(1.f, eY), sigS = ldexpf(1.f, eS);
+                    const float c1 = s_c[2 * q - 1], c0 = s_c[2 * q - 2];
+                    for (int g = half; g < nkg; g += 2) {
+                        float dr[8], di[8], xr[8], xi[8];
+                        ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+                        ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+                        if (r < NP) {
+    #pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                dr[c] *= fY;
+                                di[c] *= fY;
+                            }
+                            put8(sm, oBT, plane, NP, r, g, dr, di, sigY, bad);
+    #pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                dr[c] = c1 * xr[c] + ((8 * g + c == r && r < m) ? c0 : 0.f);
+                                di[c] = c1 * xi[c];
+                            }
+                            put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
+                        }
+                    }
+                    xt_sync();
+                }
+                for (int j = q - 2; j >= 0 && !failed; --j) {
+                    if (threadIdx.x == 0) {
+                        tc_fence_after();
+                        issue_cprod(aA, aBT, plane, NP, T0re, T0im);
+                        mma_commit(&bar);
+                    }
+                    if (!mma_wait()) { failed = true; break; }
+                    const float f = ldexpf(1.f, -(eS + eY)), sigS = ldexpf(1.f, eS);
+                    const float c1 = s_c[2 * j + 1], c0 = s_c[2 * j];
+                    for (int g = half; g < nkg; g += 2) {
+                        float dr[8], di[8], xr[8], xi[8];
+                        ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+                        ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+    #pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            dr[c] = fmaf(dr[c], f, c1 * xr[c]) + ((8 * g + c == r && r < m) ? c0 : 0.f);
+                            di[c] = fmaf(di[c], f, c1 * xi[c]);
+                        }
+                        if (j > 0) {
+                            if (r < NP) put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
+                        } else {
+                            finish8(g, dr, di);
+                        }
+                    }
+                    xt_sync();
+                }
+                if (failed) break;
+            } else {
+                // degree 1: T(X) = I + X
+                for (int g = half; g < nkg; g += 2) {
+                    float xr[8], xi[8];
+                    ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
+    #pragma unroll
+                    for (int c = 0; c < 8; ++c) xr[c] += (8 * g + c == r && r < m) ? 1.f : 0.f;
+                    finish8(g, xr, xi);
+                }
+                xt_sync();
             }
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = make_float2((float)Da[e].x, (float)Da[e].y);
-            __syncthreads();
+
+            // ---- squarings
+            if (s > 0 && !sq64) {
+                // S^T from the product with the identity, into the B^T planes (scale carried over)
+                if (threadIdx.x == 0) {
+                    tc_fence_after();
+                    issue_ident(aBT, aA, plane, NP, T1re, T1im);
+                    mma_commit(&bar);
+                }
+                if (!mma_wait()) { failed = true; break; }
+                for (int g = half; g < nkg; g += 2) {
+                    float dr[8], di[8];
+                    ld_acc8(R1re + 8 * g, R1im + 8 * g, dr, di);
+                    if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
+                }
+                xt_sync();
+                const float f = ldexpf(1.f, -2 * eQ), sigQ = ldexpf(1.f, eQ);
+                for (int i = 1; i <= s && !failed; ++i) {
+                    const bool last = i == s;
+                    if (threadIdx.x == 0) {
+                        tc_fence_after();
+                        issue_cprod(aA, aBT, plane, NP, T0re, T0im);                // S^2
+                        if (!last) issue_cprod(aBT, aA, plane, NP, T1re, T1im);    // (S^2)^T
+                        mma_commit(&bar);
+                    }
+                    if (!mma_wait()) { failed = true; break; }
+                    for (int g = half; g < nkg; g += 2) {
+                        float dr[8], di[8];
+                        ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
+    #pragma unroll
+                        for (int c = 0; c < 8; ++c) {
+                            dr[c] *= f;
+                            di[c] *= f;
+                        }
+                        if (last) {
+                            if (r < m) {
+    #pragma unroll
+                                for (int c = 0; c < 8; ++c)
+                                    if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(dr[c], di[c]);
+                            }
+                        } else {
+                            float tr[8], ti[8];
+                            ld_acc8(R1re + 8 * g, R1im + 8 * g, tr, ti);
+                            if (r < NP) {
+                                put8(sm, oA, plane, NP, r, g, dr, di, sigQ, bad);
+    #pragma unroll
+                                for (int c = 0; c < 8; ++c) {
+                                    tr[c] *= f;
+                                    ti[c] *= f;
+                                }
+                                put8(sm, oBT, plane, NP, r, g, tr, ti, sigQ, bad);
+                            }
+                        }
+                    }
+                    xt_sync();
+                }
+                if (failed) break;
+            } else if (sq64) {
+                // FP64 squaring chain on the CUDA cores
+                double2* Da = D0;
+                double2* Db = D1;
+                for (int i = 0; i < s; ++i) {
+                    for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                        const int row = (int)(e / m), col = (int)(e - (size_t)row * m);
+                        double2 acc = make_double2(0.0, 0.0);
+                        for (int kk = 0; kk < m; ++kk) {
+                            const double2 a = Da[(size_t)row * m + kk], b = Da[(size_t)kk * m + col];
+                            acc.x = fma(a.x, b.x, fma(-a.y, b.y, acc.x));
+                            acc.y = fma(a.x, b.y, fma(a.y, b.x, acc.y));
+                        }
+                        Db[e] = acc;
+                    }
+                    __syncthreads();
+                    double2* t = Da;
+                    Da = Db;
+                    Db = t;
+                }
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) Uo[e] = make_float2((float)Da[e].x, (float)Da[e].y);
+                __syncthreads();
+            }
         }
     }
     if (bad) atomicOr(P.status, ST_RANGE);

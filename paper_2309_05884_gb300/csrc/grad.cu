@@ -108,218 +108,234 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        int bi, kw, k;  // block; window slot (psi_{k-1} in slot kw, lam_k in slot kw+1); slice 1..N
+    __shared__ int s_list[GRAD_THREADS];
+    __shared__ int s_nl;
+    __shared__ int s_wc[32];
+    // slices this launch owns: not those of the reverse-mode kernel (>= 2^REV_MIN_SUB sub-slices) nor
+    // the unsplit slices of register-sized blocks (grad_fast.cu)
+    auto want = [&](long long it) -> bool {
+        int bi;
+        long long k;
         if (whole) {
-            const int2 it = P.items[item];
-            bi = it.x;
-            kw = it.y;
-            k = it.y + 1;
+            const int2 e = P.items[it];
+            bi = e.x;
+            k = e.y;
         } else {
-            bi = (int)(item / NK);
-            kw = (int)(item % NK);
-            k = P.k0 + kw + 1;
+            bi = (int)(it / NK);
+            k = P.k0 + it % NK;
         }
-        const DevBlock& B = P.blocks[bi];
-        const int m = B.m, c = B.c;
-        const size_t mm = (size_t)m * m;
-        const T tau = (T)B.dt;
-        if (threadIdx.x == 0) {
-            double beta = B.h0_norm1;
-            for (int j = 0; j < nc; ++j) {
-                const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
-                s_uk[j] = isfinite(uk) ? uk : 0.0;
-                beta += fabs(s_uk[j]) * B.hc_norm1[j];
+        const DevBlock& Bw = P.blocks[bi];
+        const int sub = P.grad_mode == 0 ? slice_halvings(slice_beta(P, Bw, u, k), theta, MAX_SUB_LOG2) : 0;
+        return sub < REV_MIN_SUB && !(sub == 0 && Bw.m <= fast_m);
+    };
+    for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
+        const int nl = s_nl;
+        for (int li = 0; li < nl; ++li) {
+            const long long item = (long long)blockIdx.x + (lb + s_list[li]) * gridDim.x;
+            int bi, kw, k;  // block; window slot (psi_{k-1} in slot kw, lam_k in slot kw+1); slice 1..N
+            if (whole) {
+                const int2 it = P.items[item];
+                bi = it.x;
+                kw = it.y;
+                k = it.y + 1;
+            } else {
+                bi = (int)(item / NK);
+                kw = (int)(item % NK);
+                k = P.k0 + kw + 1;
             }
-            beta *= B.dt;
-            int Pt = 0, sub = 0;
-            if (P.grad_mode == 0) {
-                while (beta > theta && sub < MAX_SUB_LOG2) { beta *= 0.5; ++sub; }
-                double term = beta;  // beta^{P+1}/(P+1)! at P = 0
-                while (Pt < PM && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
-                if (term > tol || beta > theta) atomicOr(P.status, ST_SERIES_CAP);
-            }
-            s_P = Pt;
-            s_sub = sub;
-        }
-        __syncthreads();
-        if (s_sub >= REV_MIN_SUB) {  // large-norm slice: the reverse-mode kernel (grad_rev.cu) owns it
-            __syncthreads();
-            continue;
-        }
-        if (s_sub == 0 && m <= fast_m) {  // unsplit slice of a register-sized block: grad_fast.cu owns it
-            __syncthreads();
-            continue;
-        }
-        const int Pt = s_P;
-        const int nsub = 1 << s_sub;
-        const T tau_s = tau / (T)nsub;
-        const cx<T>* H = reinterpret_cast<const cx<T>*>(P.H) + B.h_off;
-        if (P.grad_mode == 0) {
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                cx<T> h = H[e];
+            const DevBlock& B = P.blocks[bi];
+            const int m = B.m, c = B.c;
+            const size_t mm = (size_t)m * m;
+            const T tau = (T)B.dt;
+            if (threadIdx.x == 0) {
+                double beta = B.h0_norm1;
                 for (int j = 0; j < nc; ++j) {
-                    const cx<T> hc = H[(size_t)(1 + j) * mm + e];
-                    const T uj = (T)s_uk[j];
-                    h.x = fma(uj, hc.x, h.x);
-                    h.y = fma(uj, hc.y, h.y);
+                    const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
+                    s_uk[j] = isfinite(uk) ? uk : 0.0;
+                    beta += fabs(s_uk[j]) * B.hc_norm1[j];
                 }
-                A[e] = cmul_mis<T>(h, tau_s);
-            }
-        }
-        // per-thread partial sums in the working precision (a thread adds ~m^2/blockDim terms);
-        // the cross-thread reduction below is FP64
-        T accr[8], acci[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) accr[j] = acci[j] = (T)0;
-        __syncthreads();
-        for (int r0 = 0; r0 < c; r0 += CG) {
-            const int cg = (c - r0) < CG ? (c - r0) : CG;
-            // V[q][r] at V + (q*CG + r)*m ; Z likewise ; W[r] at W + r*m ; Psub[i][r] at Psub + (i*CG + r)*m
-            const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
-            for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
-                const int r = e / m, a = e - r * m;
-                const cx<T> x = psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a];
-                if (nsub == 1) V[(size_t)r * m + a] = x; else Psub[(size_t)r * m + a] = x;
-                W[(size_t)r * m + a] = lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a];
+                beta *= B.dt;
+                int Pt = 0, sub = 0;
+                if (P.grad_mode == 0) {
+                    while (beta > theta && sub < MAX_SUB_LOG2) { beta *= 0.5; ++sub; }
+                    double term = beta;  // beta^{P+1}/(P+1)! at P = 0
+                    while (Pt < PM && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
+                    if (term > tol || beta > theta) atomicOr(P.status, ST_SERIES_CAP);
+                }
+                s_P = Pt;
+                s_sub = sub;
             }
             __syncthreads();
-            // forward sub-states psi^(i+1) = sum_q A^q psi^(i) / q!  (split slices only)
-            for (int i = 0; i + 1 < nsub; ++i) {
+            const int Pt = s_P;
+            const int nsub = 1 << s_sub;
+            const T tau_s = tau / (T)nsub;
+            const cx<T>* H = reinterpret_cast<const cx<T>*>(P.H) + B.h_off;
+            if (P.grad_mode == 0) {
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                    cx<T> h = H[e];
+                    for (int j = 0; j < nc; ++j) {
+                        const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                        const T uj = (T)s_uk[j];
+                        h.x = fma(uj, hc.x, h.x);
+                        h.y = fma(uj, hc.y, h.y);
+                    }
+                    A[e] = cmul_mis<T>(h, tau_s);
+                }
+            }
+            // per-thread partial sums in the working precision (a thread adds ~m^2/blockDim terms);
+            // the cross-thread reduction below is FP64
+            T accr[8], acci[8];
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) accr[j] = acci[j] = (T)0;
+            __syncthreads();
+            for (int r0 = 0; r0 < c; r0 += CG) {
+                const int cg = (c - r0) < CG ? (c - r0) : CG;
+                // V[q][r] at V + (q*CG + r)*m ; Z likewise ; W[r] at W + r*m ; Psub[i][r] at Psub + (i*CG + r)*m
+                const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
                 for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
                     const int r = e / m, a = e - r * m;
-                    const cx<T> x = Psub[((size_t)i * CG + r) * m + a];
-                    V[(size_t)r * m + a] = x;
-                    Psub[((size_t)(i + 1) * CG + r) * m + a] = x;
+                    const cx<T> x = psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a];
+                    if (nsub == 1) V[(size_t)r * m + a] = x; else Psub[(size_t)r * m + a] = x;
+                    W[(size_t)r * m + a] = lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a];
                 }
                 __syncthreads();
-                for (int q = 1; q <= Pt; ++q) {
-                    cx<T>* ys[2 * CG];
-                    const cx<T>* xs[2 * CG];
-                    T sg[2 * CG];
-#pragma unroll
-                    for (int r = 0; r < 2 * CG; ++r) {
-                        const int rr = r < cg ? r : 0;
-                        xs[r] = V + ((size_t)(q - 1) * CG + rr) * m;
-                        ys[r] = V + ((size_t)q * CG + rr) * m;
-                        sg[r] = (T)1;
-                    }
-                    cta_gemv_multi<T, 2 * CG>(ys, A, xs, sg, cg, m);
-                    const T cf = (T)s_if[q];
+                // forward sub-states psi^(i+1) = sum_q A^q psi^(i) / q!  (split slices only)
+                for (int i = 0; i + 1 < nsub; ++i) {
                     for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
                         const int r = e / m, a = e - r * m;
-                        cx<T>& d = Psub[((size_t)(i + 1) * CG + r) * m + a];
-                        const cx<T> v = V[((size_t)q * CG + r) * m + a];
-                        d.x = fma(cf, v.x, d.x);
-                        d.y = fma(cf, v.y, d.y);
+                        const cx<T> x = Psub[((size_t)i * CG + r) * m + a];
+                        V[(size_t)r * m + a] = x;
+                        Psub[((size_t)(i + 1) * CG + r) * m + a] = x;
                     }
                     __syncthreads();
-                }
-            }
-            for (int isub = nsub - 1; isub >= 0; --isub) {
-                if (nsub > 1) {
-                    for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
-                        const int r = e / m, a = e - r * m;
-                        V[(size_t)r * m + a] = Psub[((size_t)isub * CG + r) * m + a];
-                    }
-                }
-                for (int e = threadIdx.x; e < (Pt + 1) * CG * m; e += blockDim.x) Z[e] = mk<T>(0, 0);
-                for (int e = threadIdx.x; e < CG * m; e += blockDim.x) Ln[e] = mk<T>(0, 0);
-                __syncthreads();
-                for (int p = 0; p <= Pt; ++p) {
-                    // z_q += w_p / (p+q+1)!  for q <= P-p ; the previous sub-slice's costate += w_p / p!
-                    for (int e = threadIdx.x; e < (Pt - p + 1) * cg * m; e += blockDim.x) {
-                        const int q = e / (cg * m);
-                        const int ra = e - q * cg * m;
-                        const T cf = (T)s_if[p + q + 1];
-                        cx<T>& z = Z[(size_t)q * CG * m + ra];
-                        const cx<T> w = W[ra];
-                        z.x = fma(cf, w.x, z.x);
-                        z.y = fma(cf, w.y, z.y);
-                        if (q == 0 && nsub > 1) {
-                            const T cl = (T)s_if[p];
-                            Ln[ra].x = fma(cl, w.x, Ln[ra].x);
-                            Ln[ra].y = fma(cl, w.y, Ln[ra].y);
-                        }
-                    }
-                    __syncthreads();
-                    if (p < Pt) {
-                        // one pass over A: v_{p+1} = A v_p and w_{p+1} = -A w_p for every copy of the group
+                    for (int q = 1; q <= Pt; ++q) {
                         cx<T>* ys[2 * CG];
                         const cx<T>* xs[2 * CG];
                         T sg[2 * CG];
-#pragma unroll
-                        for (int r = 0; r < CG; ++r) {
-                            // v vectors in slots [0, cg), w vectors in [cg, 2cg); unused slots are never read
+    #pragma unroll
+                        for (int r = 0; r < 2 * CG; ++r) {
                             const int rr = r < cg ? r : 0;
-                            xs[r] = V + ((size_t)p * CG + rr) * m;
-                            ys[r] = V + ((size_t)(p + 1) * CG + rr) * m;
+                            xs[r] = V + ((size_t)(q - 1) * CG + rr) * m;
+                            ys[r] = V + ((size_t)q * CG + rr) * m;
                             sg[r] = (T)1;
                         }
-#pragma unroll
-                        for (int r = 0; r < CG; ++r) {
-                            const int rr = r < cg ? r : 0;
-                            xs[CG + r] = W + (size_t)rr * m;
-                            ys[CG + r] = Wn + (size_t)rr * m;
-                            sg[CG + r] = (T)-1;
+                        cta_gemv_multi<T, 2 * CG>(ys, A, xs, sg, cg, m);
+                        const T cf = (T)s_if[q];
+                        for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
+                            const int r = e / m, a = e - r * m;
+                            cx<T>& d = Psub[((size_t)(i + 1) * CG + r) * m + a];
+                            const cx<T> v = V[((size_t)q * CG + r) * m + a];
+                            d.x = fma(cf, v.x, d.x);
+                            d.y = fma(cf, v.y, d.y);
                         }
-                        if (cg < CG) {  // pack the w vectors right after the v vectors
-                            for (int r = 0; r < cg; ++r) {
-                                xs[cg + r] = xs[CG + r];
-                                ys[cg + r] = ys[CG + r];
-                                sg[cg + r] = (T)-1;
+                        __syncthreads();
+                    }
+                }
+                for (int isub = nsub - 1; isub >= 0; --isub) {
+                    if (nsub > 1) {
+                        for (int e = threadIdx.x; e < cg * m; e += blockDim.x) {
+                            const int r = e / m, a = e - r * m;
+                            V[(size_t)r * m + a] = Psub[((size_t)isub * CG + r) * m + a];
+                        }
+                    }
+                    for (int e = threadIdx.x; e < (Pt + 1) * CG * m; e += blockDim.x) Z[e] = mk<T>(0, 0);
+                    for (int e = threadIdx.x; e < CG * m; e += blockDim.x) Ln[e] = mk<T>(0, 0);
+                    __syncthreads();
+                    for (int p = 0; p <= Pt; ++p) {
+                        // z_q += w_p / (p+q+1)!  for q <= P-p ; the previous sub-slice's costate += w_p / p!
+                        for (int e = threadIdx.x; e < (Pt - p + 1) * cg * m; e += blockDim.x) {
+                            const int q = e / (cg * m);
+                            const int ra = e - q * cg * m;
+                            const T cf = (T)s_if[p + q + 1];
+                            cx<T>& z = Z[(size_t)q * CG * m + ra];
+                            const cx<T> w = W[ra];
+                            z.x = fma(cf, w.x, z.x);
+                            z.y = fma(cf, w.y, z.y);
+                            if (q == 0 && nsub > 1) {
+                                const T cl = (T)s_if[p];
+                                Ln[ra].x = fma(cl, w.x, Ln[ra].x);
+                                Ln[ra].y = fma(cl, w.y, Ln[ra].y);
                             }
                         }
-                        cta_gemv_multi<T, 2 * CG>(ys, A, xs, sg, 2 * cg, m);
-                        cx<T>* t = W; W = Wn; Wn = t;
+                        __syncthreads();
+                        if (p < Pt) {
+                            // one pass over A: v_{p+1} = A v_p and w_{p+1} = -A w_p for every copy of the group
+                            cx<T>* ys[2 * CG];
+                            const cx<T>* xs[2 * CG];
+                            T sg[2 * CG];
+    #pragma unroll
+                            for (int r = 0; r < CG; ++r) {
+                                // v vectors in slots [0, cg), w vectors in [cg, 2cg); unused slots are never read
+                                const int rr = r < cg ? r : 0;
+                                xs[r] = V + ((size_t)p * CG + rr) * m;
+                                ys[r] = V + ((size_t)(p + 1) * CG + rr) * m;
+                                sg[r] = (T)1;
+                            }
+    #pragma unroll
+                            for (int r = 0; r < CG; ++r) {
+                                const int rr = r < cg ? r : 0;
+                                xs[CG + r] = W + (size_t)rr * m;
+                                ys[CG + r] = Wn + (size_t)rr * m;
+                                sg[CG + r] = (T)-1;
+                            }
+                            if (cg < CG) {  // pack the w vectors right after the v vectors
+                                for (int r = 0; r < cg; ++r) {
+                                    xs[cg + r] = xs[CG + r];
+                                    ys[cg + r] = ys[CG + r];
+                                    sg[cg + r] = (T)-1;
+                                }
+                            }
+                            cta_gemv_multi<T, 2 * CG>(ys, A, xs, sg, 2 * cg, m);
+                            cx<T>* t = W; W = Wn; Wn = t;
+                        }
+                    }
+                // contraction with every Hc_j: sum_{a,b} Hc_j[a][b] sum_{q,r} conj(Z_qr[a]) V_qr[b]
+                for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
+                    const int a = (int)(e / m), b = (int)(e - (size_t)a * m);
+                    cx<T> Mab = mk<T>(0, 0);
+                    for (int q = 0; q <= Pt; ++q)
+                        for (int r = 0; r < cg; ++r)
+                            cfma_conj<T>(Mab, Z[((size_t)q * CG + r) * m + a], V[((size_t)q * CG + r) * m + b]);
+    #pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j < nc) {
+                            const cx<T> hc = H[(size_t)(1 + j) * mm + e];
+                            accr[j] = fma(hc.x, Mab.x, fma(-hc.y, Mab.y, accr[j]));
+                            acci[j] = fma(hc.x, Mab.y, fma(hc.y, Mab.x, acci[j]));
+                        }
                     }
                 }
-            // contraction with every Hc_j: sum_{a,b} Hc_j[a][b] sum_{q,r} conj(Z_qr[a]) V_qr[b]
-            for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
-                const int a = (int)(e / m), b = (int)(e - (size_t)a * m);
-                cx<T> Mab = mk<T>(0, 0);
-                for (int q = 0; q <= Pt; ++q)
-                    for (int r = 0; r < cg; ++r)
-                        cfma_conj<T>(Mab, Z[((size_t)q * CG + r) * m + a], V[((size_t)q * CG + r) * m + b]);
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j < nc) {
-                        const cx<T> hc = H[(size_t)(1 + j) * mm + e];
-                        accr[j] = fma(hc.x, Mab.x, fma(-hc.y, Mab.y, accr[j]));
-                        acci[j] = fma(hc.x, Mab.y, fma(hc.y, Mab.x, acci[j]));
-                    }
-                }
-            }
-                __syncthreads();
-                if (nsub > 1) {  // costate at the start of this sub-slice
-                    for (int e = threadIdx.x; e < cg * m; e += blockDim.x) W[e] = Ln[e];
                     __syncthreads();
+                    if (nsub > 1) {  // costate at the start of this sub-slice
+                        for (int e = threadIdx.x; e < cg * m; e += blockDim.x) W[e] = Ln[e];
+                        __syncthreads();
+                    }
                 }
             }
-        }
-        // block reduction of the nc complex sums; then multiply by -i tau / 2^s
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j >= nc) break;
-            double xr = (double)accr[j], xi = (double)acci[j];
-            for (int off = 16; off > 0; off >>= 1) {
-                xr += __shfl_xor_sync(0xffffffffu, xr, off);
-                xi += __shfl_xor_sync(0xffffffffu, xi, off);
+            // block reduction of the nc complex sums; then multiply by -i tau / 2^s
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j >= nc) break;
+                double xr = (double)accr[j], xi = (double)acci[j];
+                for (int off = 16; off > 0; off >>= 1) {
+                    xr += __shfl_xor_sync(0xffffffffu, xr, off);
+                    xi += __shfl_xor_sync(0xffffffffu, xi, off);
+                }
+                if (lane == 0) { red[warp][j][0] = xr; red[warp][j][1] = xi; }
             }
-            if (lane == 0) { red[warp][j][0] = xr; red[warp][j][1] = xi; }
+            __syncthreads();
+            if (threadIdx.x < nc) {
+                double xr = 0.0, xi = 0.0;
+                for (int w = 0; w < GRAD_THREADS / 32; ++w) { xr += red[w][threadIdx.x][0]; xi += red[w][threadIdx.x][1]; }
+                // (-i tau) (xr + i xi) = tau xi - i tau xr
+                const double ts = B.dt / (double)nsub;
+                double2 o;
+                o.x = ts * xi;
+                o.y = -ts * xr;
+                partial[(size_t)(B.part_off + k - 1) * nc + threadIdx.x] = o;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x < nc) {
-            double xr = 0.0, xi = 0.0;
-            for (int w = 0; w < GRAD_THREADS / 32; ++w) { xr += red[w][threadIdx.x][0]; xi += red[w][threadIdx.x][1]; }
-            // (-i tau) (xr + i xi) = tau xi - i tau xr
-            const double ts = B.dt / (double)nsub;
-            double2 o;
-            o.x = ts * xi;
-            o.y = -ts * xr;
-            partial[(size_t)(B.part_off + k - 1) * nc + threadIdx.x] = o;
-        }
-        __syncthreads();
     }
 }
 

@@ -199,7 +199,7 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
     S.Z = S.X + (size_t)(GF_PM + 1) * GF_NVM * GF_VL;
     __shared__ float s_if[GF_PM + 2];
     __shared__ float s_uk[8];
-    __shared__ int s_P, s_skip;
+    __shared__ int s_P;
     __shared__ double red[GF_THREADS / 32][8][2];
     // per-thread contraction sums (re, im of each control), kept out of registers during the chains
     __shared__ float2 s_acc[8][GF_THREADS];
@@ -220,140 +220,160 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
     const int NK = P.nk;
     const bool whole = P.nk < 0;
     const long long total = whole ? P.n_items : (long long)NK * P.nb;
-    for (long long item = blockIdx.x; item < total; item += gridDim.x) {
-        int bi, kw, k;
+    __shared__ int s_list[GF_THREADS];
+    __shared__ int s_nl;
+    __shared__ int s_wc[32];
+    // slices this launch owns: blocks of size (m_lo, MT], slices that need no sub-slicing
+    auto want = [&](long long it) -> bool {
+        int bi;
+        long long k;
         if (whole) {
-            const int2 it = P.items[item];
-            bi = it.x;
-            kw = it.y;
-            k = it.y + 1;
+            const int2 e = P.items[it];
+            bi = e.x;
+            k = e.y;
         } else {
-            bi = (int)(item / NK);
-            kw = (int)(item % NK);
-            k = P.k0 + kw + 1;
+            bi = (int)(it / NK);
+            k = P.k0 + it % NK;
         }
-        const DevBlock& B = P.blocks[bi];
-        const int m = B.m, c = B.c;
-        if (m <= m_lo || m > MT) continue;  // another launch owns this block size
-        __syncthreads();                     // the previous item's readers of s_* are done
-        if (threadIdx.x == 0) {
-            double beta = B.h0_norm1;
-            for (int j = 0; j < nc; ++j) {
-                const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
-                const double x = isfinite(uk) ? uk : 0.0;
-                s_uk[j] = (float)x;
-                beta += fabs(x) * B.hc_norm1[j];
+        const DevBlock& Bw = P.blocks[bi];
+        if (Bw.m <= m_lo || Bw.m > MT) return false;
+        return P.grad_mode != 0 || slice_halvings(slice_beta(P, Bw, u, k), theta, GF_SUB_MAX) == 0;
+    };
+    for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
+        const int nl = s_nl;
+        for (int li = 0; li < nl; ++li) {
+            const long long item = (long long)blockIdx.x + (lb + s_list[li]) * gridDim.x;
+            int bi, kw, k;
+            if (whole) {
+                const int2 it = P.items[item];
+                bi = it.x;
+                kw = it.y;
+                k = it.y + 1;
+            } else {
+                bi = (int)(item / NK);
+                kw = (int)(item % NK);
+                k = P.k0 + kw + 1;
             }
-            beta *= B.dt;
-            int Pt = 0, sub = 0;
-            if (P.grad_mode == 0) {
-                while (beta > theta && sub < GF_SUB_MAX) { beta *= 0.5; ++sub; }
-                double term = beta;
-                while (Pt < GF_PM && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
-                if (sub == 0 && term > tol) atomicOr(P.status, ST_SERIES_CAP);
-            }
-            s_P = Pt;
-            s_skip = sub > 0;  // split slices: grad.cu (sub-slices) or grad_rev.cu (reverse mode)
-            if (P.stats && sub == 0)
-                atomicAdd(P.stats + 3, (unsigned long long)m * m * (unsigned long long)(c * (3 * Pt + 1) + nc));
-        }
-        __syncthreads();
-        if (s_skip) continue;
-        const int Pt = s_P;
-        const size_t mm = (size_t)m * m;
-        const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
-        const float tau = (float)B.dt;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) s_acc[j][threadIdx.x] = f2(0.f, 0.f);
-
-        for (int r0 = 0; r0 < c; r0 += GF_CG) {
-            const int cg = (c - r0) < GF_CG ? (c - r0) : GF_CG;
-            const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
-            // tile of A (grad_mode 0): rows warp RW + rs + 4 i, columns gf_col(cp, cc); assembled per
-            // copy group, one pass per matrix so that a tile's loads are in flight together
-            float2 At[RPT][CPT];
-#pragma unroll
-            for (int i = 0; i < RPT; ++i)
-#pragma unroll
-                for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(0.f, 0.f);
-            if (P.grad_mode == 0) {
-#pragma unroll
-                for (int i = 0; i < RPT; ++i) {
-                    const int a = warp * RW + rs + 4 * i;
-#pragma unroll
-                    for (int cc = 0; cc < CPT; ++cc) {
-                        const int b = gf_col(cp, cc);
-                        if (a < m && b < m) At[i][cc] = H[(size_t)a * m + b];
-                    }
-                }
+            const DevBlock& B = P.blocks[bi];
+            const int m = B.m, c = B.c;
+            __syncthreads();  // the previous item's readers of s_* are done
+            if (threadIdx.x == 0) {
+                double beta = B.h0_norm1;
                 for (int j = 0; j < nc; ++j) {
-                    const float2* Hj = H + (size_t)(1 + j) * mm;
-                    const float uj = s_uk[j];
-#pragma unroll
+                    const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
+                    const double x = isfinite(uk) ? uk : 0.0;
+                    s_uk[j] = (float)x;
+                    beta += fabs(x) * B.hc_norm1[j];
+                }
+                beta *= B.dt;
+                int Pt = 0, sub = 0;
+                if (P.grad_mode == 0) {
+                    while (beta > theta && sub < GF_SUB_MAX) { beta *= 0.5; ++sub; }
+                    double term = beta;
+                    while (Pt < GF_PM && term > tol) { ++Pt; term *= beta / (double)(Pt + 1); }
+                    if (sub == 0 && term > tol) atomicOr(P.status, ST_SERIES_CAP);
+                }
+                s_P = Pt;
+                if (P.stats)
+                    atomicAdd(P.stats + 3, (unsigned long long)m * m * (unsigned long long)(c * (3 * Pt + 1) + nc));
+            }
+            __syncthreads();
+            const int Pt = s_P;
+            const size_t mm = (size_t)m * m;
+            const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
+            const float tau = (float)B.dt;
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) s_acc[j][threadIdx.x] = f2(0.f, 0.f);
+
+            for (int r0 = 0; r0 < c; r0 += GF_CG) {
+                const int cg = (c - r0) < GF_CG ? (c - r0) : GF_CG;
+                const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
+                // tile of A (grad_mode 0): rows warp RW + rs + 4 i, columns gf_col(cp, cc); assembled per
+                // copy group, one pass per matrix so that a tile's loads are in flight together
+                float2 At[RPT][CPT];
+    #pragma unroll
+                for (int i = 0; i < RPT; ++i)
+    #pragma unroll
+                    for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(0.f, 0.f);
+                if (P.grad_mode == 0) {
+    #pragma unroll
                     for (int i = 0; i < RPT; ++i) {
                         const int a = warp * RW + rs + 4 * i;
-#pragma unroll
+    #pragma unroll
                         for (int cc = 0; cc < CPT; ++cc) {
                             const int b = gf_col(cp, cc);
-                            if (a < m && b < m) {
-                                const float2 hc = Hj[(size_t)a * m + b];
-                                At[i][cc].x = fmaf(uj, hc.x, At[i][cc].x);
-                                At[i][cc].y = fmaf(uj, hc.y, At[i][cc].y);
+                            if (a < m && b < m) At[i][cc] = H[(size_t)a * m + b];
+                        }
+                    }
+                    for (int j = 0; j < nc; ++j) {
+                        const float2* Hj = H + (size_t)(1 + j) * mm;
+                        const float uj = s_uk[j];
+    #pragma unroll
+                        for (int i = 0; i < RPT; ++i) {
+                            const int a = warp * RW + rs + 4 * i;
+    #pragma unroll
+                            for (int cc = 0; cc < CPT; ++cc) {
+                                const int b = gf_col(cp, cc);
+                                if (a < m && b < m) {
+                                    const float2 hc = Hj[(size_t)a * m + b];
+                                    At[i][cc].x = fmaf(uj, hc.x, At[i][cc].x);
+                                    At[i][cc].y = fmaf(uj, hc.y, At[i][cc].y);
+                                }
                             }
                         }
                     }
+    #pragma unroll
+                    for (int i = 0; i < RPT; ++i)
+    #pragma unroll
+                        for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(tau * At[i][cc].y, -tau * At[i][cc].x);  // -i tau h
                 }
-#pragma unroll
-                for (int i = 0; i < RPT; ++i)
-#pragma unroll
-                    for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(tau * At[i][cc].y, -tau * At[i][cc].x);  // -i tau h
-            }
-            // v_0 = psi, w_0 = lam of the group's copies (full length, zero tail); Z[0..Pt] = 0
-            for (int e = threadIdx.x; e < GF_CG * GF_VL; e += GF_THREADS) {
-                const int r = e / GF_VL, a = e % GF_VL;
-                const bool in = r < cg && a < m;
-                S.x(0, r)[a] = in ? psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a] : f2(0.f, 0.f);
-                S.x(0, GF_CG + r)[a] = in ? lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a]
-                                          : f2(0.f, 0.f);
-            }
-            for (int e = threadIdx.x; e < (Pt + 1) * GF_CG * GF_VL; e += GF_THREADS) S.Z[e] = f2(0.f, 0.f);
-            __syncthreads();
-            if (cg == 2) {
-                gf_group<MT, 4>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
-            } else {
-                // one copy: the w vectors live in slot CG = 1 of the NV = 2 layout; move w_0 there
-                for (int e = threadIdx.x; e < GF_VL; e += GF_THREADS) S.x(0, 1)[e] = S.x(0, GF_CG)[e];
+                // v_0 = psi, w_0 = lam of the group's copies (full length, zero tail); Z[0..Pt] = 0
+                for (int e = threadIdx.x; e < GF_CG * GF_VL; e += GF_THREADS) {
+                    const int r = e / GF_VL, a = e % GF_VL;
+                    const bool in = r < cg && a < m;
+                    S.x(0, r)[a] = in ? psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a] : f2(0.f, 0.f);
+                    S.x(0, GF_CG + r)[a] = in ? lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a]
+                                              : f2(0.f, 0.f);
+                }
+                for (int e = threadIdx.x; e < (Pt + 1) * GF_CG * GF_VL; e += GF_THREADS) S.Z[e] = f2(0.f, 0.f);
                 __syncthreads();
-                gf_group<MT, 2>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
+                if (cg == 2) {
+                    gf_group<MT, 4>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
+                } else {
+                    // one copy: the w vectors live in slot CG = 1 of the NV = 2 layout; move w_0 there
+                    for (int e = threadIdx.x; e < GF_VL; e += GF_THREADS) S.x(0, 1)[e] = S.x(0, GF_CG)[e];
+                    __syncthreads();
+                    gf_group<MT, 2>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
+                }
+                __syncthreads();  // X, Z are refilled by the next copy group
             }
-            __syncthreads();  // X, Z are refilled by the next copy group
-        }
-        // block reduction of the nc complex sums in FP64 (the per-thread sums cancel strongly when
-        // the gradient is small, so they are added without further FP32 rounding); then -i tau
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            if (j >= nc) break;
-            double xr = (double)s_acc[j][threadIdx.x].x, xi = (double)s_acc[j][threadIdx.x].y;
-            for (int off = 16; off > 0; off >>= 1) {
-                xr += __shfl_xor_sync(0xffffffffu, xr, off);
-                xi += __shfl_xor_sync(0xffffffffu, xi, off);
+            // block reduction of the nc complex sums in FP64 (the per-thread sums cancel strongly when
+            // the gradient is small, so they are added without further FP32 rounding); then -i tau
+    #pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                if (j >= nc) break;
+                double xr = (double)s_acc[j][threadIdx.x].x, xi = (double)s_acc[j][threadIdx.x].y;
+                for (int off = 16; off > 0; off >>= 1) {
+                    xr += __shfl_xor_sync(0xffffffffu, xr, off);
+                    xi += __shfl_xor_sync(0xffffffffu, xi, off);
+                }
+                if (lane == 0) {
+                    red[warp][j][0] = xr;
+                    red[warp][j][1] = xi;
+                }
             }
-            if (lane == 0) {
-                red[warp][j][0] = xr;
-                red[warp][j][1] = xi;
+            __syncthreads();
+            if (threadIdx.x < nc) {
+                double xr = 0.0, xi = 0.0;
+                for (int w = 0; w < GF_THREADS / 32; ++w) {
+                    xr += red[w][threadIdx.x][0];
+                    xi += red[w][threadIdx.x][1];
+                }
+                double2 o;
+                o.x = B.dt * xi;
+                o.y = -B.dt * xr;
+                partial[(size_t)(B.part_off + k - 1) * nc + threadIdx.x] = o;
             }
-        }
-        __syncthreads();
-        if (threadIdx.x < nc) {
-            double xr = 0.0, xi = 0.0;
-            for (int w = 0; w < GF_THREADS / 32; ++w) {
-                xr += red[w][threadIdx.x][0];
-                xi += red[w][threadIdx.x][1];
-            }
-            double2 o;
-            o.x = B.dt * xi;
-            o.y = -B.dt * xr;
-            partial[(size_t)(B.part_off + k - 1) * nc + threadIdx.x] = o;
         }
     }
     (void)cp;

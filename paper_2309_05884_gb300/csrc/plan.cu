@@ -606,11 +606,12 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     }
     p->tabs.sq_f64 = o.prec == QOC_PREC_F32_ALL ? 0 : 1;
 
-    // expm size classes.  In FP32 plans the slices of blocks with 25..112 states that need no
-    // squaring go to the tensor cores; a tensor-core product errs up to about 2x an FP32 one, so
-    // slices whose squarings would amplify that stay on the tiled CUDA-core kernels, as do all other
-    // blocks (the autotuner may pick the warp-packed or other tensor-core rules)
-    if (o.prec != QOC_PREC_F64) {
+    // expm size classes.  In plans with the FP64 squaring chain the slices of blocks with 25..112
+    // states that need no squaring go to the tensor cores; a tensor-core product errs up to about 2x
+    // an FP32 one, so slices whose squarings would amplify that stay on the tiled CUDA-core kernels,
+    // as do all other blocks.  All-FP32 plans (typically large norms, where most slices are squared)
+    // keep the tiled kernels; the autotuner may pick warp-packed or tensor-core rules.
+    if (o.prec == QOC_PREC_F32) {
         p->rules.push_back({24, 0, 0});
         p->rules.push_back({112, 2, 0});
     }
