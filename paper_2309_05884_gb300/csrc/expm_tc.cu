@@ -41,7 +41,8 @@
 namespace qoc {
 namespace {
 
-constexpr int XT_THREADS = 256;  // 8 warps: warp w drains TMEM lanes 32 (w % 4).., column groups w / 4 + 2 t
+constexpr int XT_THREADS = 512;  // 16 warps: warp w drains TMEM lanes 32 (w % 4).., column groups w / 4 + 4 t
+constexpr int XT_GSTRIDE = XT_THREADS / 128;  // warps sharing a TMEM lane quarter
 constexpr int XT_MAXM = 112;
 constexpr uint64_t XT_WAIT_NS = 2000000000ull;
 
@@ -54,19 +55,22 @@ __host__ __device__ inline int xt_cs(int NP) {
 // dynamic shared memory of one CTA for operand size NP: 8 planes + the overread slack
 __host__ __device__ inline size_t xt_smem(int NP) { return ((size_t)8 * NP * NP + (size_t)(128 - NP) * NP) * 2; }
 
-// Split 8 values (scaled by sig) into FP16 hi and lo parts, packed two per word in column order.
+// Split 8 values (scaled by sig) into FP16 hi and lo parts, packed two per word in column order; a
+// pair converts in one instruction each way.  bad is set if a scaled value leaves the FP16 range.
 __device__ __forceinline__ void split8(const float (&v)[8], float sig, uint4& hi, uint4& lo, bool& bad) {
     uint32_t h[4], l[4];
+    float mx = 0.f;
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
         const float a = v[2 * i] * sig, b = v[2 * i + 1] * sig;
-        bad |= !(fabsf(a) <= 65504.f) || !(fabsf(b) <= 65504.f);
-        const __half ah = __float2half_rn(a), bh = __float2half_rn(b);
-        const __half al = __float2half_rn(a - __half2float(ah)), bl = __float2half_rn(b - __half2float(bh));
-        const __half2 hh = __halves2half2(ah, bh), ll = __halves2half2(al, bl);
+        mx = fmaxf(mx, fmaxf(fabsf(a), fabsf(b)));
+        const __half2 hh = __floats2half2_rn(a, b);
+        const float2 hf = __half22float2(hh);
+        const __half2 ll = __floats2half2_rn(a - hf.x, b - hf.y);
         h[i] = *reinterpret_cast<const uint32_t*>(&hh);
         l[i] = *reinterpret_cast<const uint32_t*>(&ll);
     }
+    bad |= !(mx <= 65504.f);
     hi = make_uint4(h[0], h[1], h[2], h[3]);
     lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
@@ -116,6 +120,10 @@ __device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t pla
                                             uint32_t d_im) {
     const uint32_t lbo = 128, sbo = (uint32_t)(NP >> 3) * 128u;
     const uint32_t pos = idesc_f16(128, NP, false), neg = idesc_f16(128, NP, true);
+    // descriptors advance by adding byte offsets / 16 to the start-address field (shared addresses
+    // stay below 2^18 bytes, so the 14-bit field never carries)
+    const uint64_t dA = smem_desc_u32(a, lbo, sbo), dB = smem_desc_u32(b, lbo, sbo);
+    const uint64_t pl = plane >> 4;
     // (lo,lo), (hi,lo), (lo,hi) first, (hi,hi) last: the accumulator rounds each addition relative to
     // its running magnitude, so the small terms are summed while it is still small and only the K/16
     // large (hi,hi) additions meet a large accumulator.  Dropping lo*lo would bias products such as
@@ -123,17 +131,16 @@ __device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t pla
     const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
+        const uint64_t ar0 = dA + ha[t] * pl, ai0 = dA + (2 + ha[t]) * pl;
+        const uint64_t br0 = dB + hb[t] * pl, bi0 = dB + (2 + hb[t]) * pl;
         for (int kk = 0; kk < NP / 16; ++kk) {
-            const uint32_t step = (uint32_t)kk * 256u;
+            const uint64_t st = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
             const int acc = (kk > 0 || t > 0);
-            const uint64_t ar = smem_desc_u32(a + ha[t] * plane + step, lbo, sbo);
-            const uint64_t ai = smem_desc_u32(a + (2 + ha[t]) * plane + step, lbo, sbo);
-            const uint64_t br = smem_desc_u32(b + hb[t] * plane + step, lbo, sbo);
-            const uint64_t bi = smem_desc_u32(b + (2 + hb[t]) * plane + step, lbo, sbo);
-            mma_f16(d_re, ar, br, pos, acc);
-            mma_f16(d_re, ai, bi, neg, 1);
-            mma_f16(d_im, ar, bi, pos, acc);
-            mma_f16(d_im, ai, br, pos, 1);
+            // the two accumulators alternate, so that consecutive MMAs do not chain on one another
+            mma_f16(d_re, ar0 + st, br0 + st, pos, acc);
+            mma_f16(d_im, ar0 + st, bi0 + st, pos, acc);
+            mma_f16(d_re, ai0 + st, bi0 + st, neg, 1);
+            mma_f16(d_im, ai0 + st, br0 + st, pos, 1);
         }
     }
 }
@@ -156,11 +163,70 @@ __device__ __forceinline__ void issue_ident(uint32_t id, uint32_t b, uint32_t pl
     }
 }
 
-// power-of-two scale exponent for entries bounded by 'bound'
+// power-of-two scale exponent for entries bounded by 'bound': 14 - ceil(log2(bound)), clamped
+__device__ __forceinline__ int xt_clamp_exp(int e) { return e < -30 ? -30 : (e > 40 ? 40 : e); }
 __device__ __forceinline__ int xt_exp_for(double bound) {
     if (!(bound > 0.0)) return 40;
-    const int e = 14 - (int)ceil(log2(bound));
-    return e < -30 ? -30 : (e > 40 ? 40 : e);
+    int ex;
+    const double mant = frexp(bound, &ex);  // bound = mant 2^ex, mant in [0.5, 1)
+    return xt_clamp_exp(14 - (mant > 0.5 ? ex : ex - 1));
+}
+// the same from log2(bound)
+__device__ __forceinline__ int xt_exp_for_log2(double lg) {
+    if (!(lg > -1e300)) return 40;
+    return xt_clamp_exp(14 - (int)ceil(lg));
+}
+
+// Xs[r LD + c] = -i sc (H0 + sum_j u_j Hc_j)[r][c] for every entry of an m x m block: consecutive
+// threads take consecutive entries (coalesced), eight per thread at a time with all 8 (1 + NC) loads
+// issued before any is used (NC: controls, -1 = nc_rt at run time).
+template <int NC>
+__device__ __forceinline__ void stage_x(float2* Xs, const float2* H, const float* uf, size_t mm, int m, int LD, float sc,
+                                        int nc_rt = 0) {
+    constexpr int NB = 4;
+    constexpr int NH = NC > 0 ? NC : 1;
+    for (size_t e0 = threadIdx.x; e0 < mm; e0 += (size_t)NB * XT_THREADS) {
+        float2 h[NB];
+        float2 hc[NH][NB];
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const size_t e = e0 + (size_t)i * XT_THREADS;
+            h[i] = e < mm ? H[e] : make_float2(0.f, 0.f);
+            if (NC > 0) {
+#pragma unroll
+                for (int j = 0; j < NH; ++j)
+                    hc[j][i] = (e < mm && j < NC) ? H[(size_t)(1 + j) * mm + e] : make_float2(0.f, 0.f);
+            }
+        }
+        if (NC > 0) {
+#pragma unroll
+            for (int j = 0; j < NH; ++j)
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    h[i].x = fmaf(uf[j], hc[j][i].x, h[i].x);
+                    h[i].y = fmaf(uf[j], hc[j][i].y, h[i].y);
+                }
+        } else if (NC < 0) {
+            for (int j = 0; j < nc_rt; ++j)
+#pragma unroll
+                for (int i = 0; i < NB; ++i) {
+                    const size_t e = e0 + (size_t)i * XT_THREADS;
+                    if (e < mm) {
+                        const float2 v = H[(size_t)(1 + j) * mm + e];
+                        h[i].x = fmaf(uf[j], v.x, h[i].x);
+                        h[i].y = fmaf(uf[j], v.y, h[i].y);
+                    }
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NB; ++i) {
+            const size_t e = e0 + (size_t)i * XT_THREADS;
+            if (e < mm) {
+                const int r = (int)(e / (size_t)m), c = (int)(e - (size_t)r * m);
+                Xs[(size_t)r * LD + c] = make_float2(h[i].y * sc, -h[i].x * sc);
+            }
+        }
+    }
 }
 
 // Make this thread's shared-memory operand writes visible to the tensor cores and its TMEM reads
@@ -183,7 +249,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
     __shared__ int s_q, s_s, s_eX, s_eY, s_eS;
     __shared__ float s_sc;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int quarter = warp & 3, half = warp >> 2;
+    const int quarter = warp & 3, gq = warp >> 2;  // gq: this warp's first column group
     const int r = 32 * quarter + lane;  // accumulator row (TMEM lane) this thread drains
     const uint32_t lane_bits = (uint32_t)(32 * quarter) << 16;
     if (warp == 0) {
@@ -230,8 +296,11 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
     __shared__ int s_nl;
     __shared__ int s_wc[32];
     // slices this launch owns: all of them, or those that need no squaring
+    // (the norm bound and the pulses of each tested slice are kept for the setup below)
+    __shared__ double s_beta[XT_THREADS];
+    __shared__ float s_ul[XT_THREADS][8];
+    __shared__ unsigned char s_nan[XT_THREADS];
     auto want = [&](long long it) -> bool {
-        if (all_items) return true;
         int bi;
         long long k;
         if (whole) {
@@ -242,7 +311,18 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             bi = cls_blocks[it / P.nk];
             k = P.k0 + it % P.nk;
         }
-        return slice_halvings(slice_beta(P, P.blocks[bi], u, k), tabs.theta_cap, P.max_sq) == 0;
+        const DevBlock& Bw = P.blocks[bi];
+        const double beta = slice_beta(P, Bw, u, k);
+        int nan = 0;
+        for (int j = 0; j < P.nc; ++j) {
+            const double x = u[(size_t)(Bw.u_row + k) * P.nc + j];
+            const int fin = isfinite(x);
+            nan |= !fin;
+            s_ul[threadIdx.x][j] = fin ? (float)x : 0.f;
+        }
+        s_beta[threadIdx.x] = beta;
+        s_nan[threadIdx.x] = (unsigned char)nan;
+        return all_items || slice_halvings(beta, tabs.theta_cap, P.max_sq) == 0;
     };
     for (long long lb = 0; !failed && cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
         const int nl = s_nl;
@@ -266,17 +346,10 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             const uint32_t oBT = 0, oA = 4 * plane;  // plane groups (byte offsets)
             const uint32_t aBT = sm_base + oBT, aA = sm_base + oA;
             if (threadIdx.x == 0) {
-                double beta = B.h0_norm1;
-                int nan = 0;
-                for (int j = 0; j < P.nc; ++j) {
-                    const double x = u[(size_t)(B.u_row + k) * P.nc + j];
-                    const int fin = isfinite(x);
-                    nan |= !fin;
-                    s_uf[j] = fin ? (float)x : 0.f;
-                    beta += fabs(fin ? x : 0.0) * B.hc_norm1[j];
-                }
-                if (nan) atomicOr(P.status, ST_NAN_PULSE);
-                beta *= B.dt;
+                const int ti = s_list[li];  // the thread that tested this slice
+                for (int j = 0; j < P.nc; ++j) s_uf[j] = s_ul[ti][j];
+                if (s_nan[ti]) atomicOr(P.status, ST_NAN_PULSE);
+                const double beta = s_beta[ti];
                 // Fewest squarings: each one doubles the error of what it squares, and a squaring here
                 // errs more than an FP32 one, so scaling further than the plan's largest norm loses
                 // more than the lower-degree polynomial gains.
@@ -296,7 +369,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                 s_sc = (float)ldexp(B.dt, -bs);
                 s_eX = xt_exp_for(bsn);
                 s_eY = xt_exp_for(bsn * bsn);
-                s_eS = xt_exp_for(exp(bsn));
+                s_eS = xt_exp_for_log2(bsn * 1.4426950408889634);  // e^beta: log2 = beta / ln 2
                 if (P.stats) {
                     const unsigned long long m3 = (unsigned long long)m * m * m;
                     atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
@@ -310,48 +383,41 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             const bool sq64 = s > 0 && tabs.sq_f64;
             float2* Uo = reinterpret_cast<float2*>(Uout) + B.u_off + (size_t)kw * B.mmp;
 
-            // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j): rows into the A planes and R1 (one read of H)
+            // ---- X = -i (tau / 2^s)(H0 + sum_j u_j Hc_j), H read once and coalesced into an FP32 buffer
+            // in the B^T planes (free until the transpose; odd row stride, so that the column reads
+            // below are free of bank conflicts); then every thread moves its rows into the A planes
+            // (split) and R1 (FP32)
             {
                 const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
                 const float sc = s_sc, sig = ldexpf(1.f, eX);
-                const bool rin = r < m;
-                for (int g = half; g < nkg; g += 2) {
-                    float2 h[8];
-    #pragma unroll
+                float2* Xs = reinterpret_cast<float2*>(sm + oBT);
+                const int LD = (m & 1) || m == NP ? m : m + 1;  // LD * m * 8 <= 4 NP^2 * 2 bytes
+                switch (P.nc) {
+                    case 0: stage_x<0>(Xs, H, s_uf, mm, m, LD, sc); break;
+                    case 1: stage_x<1>(Xs, H, s_uf, mm, m, LD, sc); break;
+                    case 2: stage_x<2>(Xs, H, s_uf, mm, m, LD, sc); break;
+                    case 3: stage_x<3>(Xs, H, s_uf, mm, m, LD, sc); break;
+                    case 4: stage_x<4>(Xs, H, s_uf, mm, m, LD, sc); break;
+                    default: stage_x<-1>(Xs, H, s_uf, mm, m, LD, sc, P.nc);
+                }
+                __syncthreads();
+                for (int g = gq; g < nkg; g += XT_GSTRIDE) {
+                    float xr[8], xi[8];
+#pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const int col = 8 * g + c;
-                        h[c] = (rin && col < m) ? H[(size_t)r * m + col] : make_float2(0.f, 0.f);
+                        const float2 x = (r < m && col < m) ? Xs[(size_t)r * LD + col] : make_float2(0.f, 0.f);
+                        xr[c] = x.x;
+                        xi[c] = x.y;
                     }
-    #pragma unroll
-                    for (int j = 0; j < 8; ++j) {  // every load of a matrix's 8 entries in flight together
-                        if (j < P.nc) {
-                            const float2* Hj = H + (size_t)(1 + j) * mm + (size_t)r * m;
-                            const float uj = s_uf[j];
-    #pragma unroll
-                            for (int c = 0; c < 8; ++c) {
-                                const int col = 8 * g + c;
-                                if (rin && col < m) {
-                                    const float2 hc = Hj[col];
-                                    h[c].x = fmaf(uj, hc.x, h[c].x);
-                                    h[c].y = fmaf(uj, hc.y, h[c].y);
-                                }
-                            }
-                        }
-                    }
-                    float xr[8], xi[8];
-    #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        xr[c] = h[c].y * sc;
-                        xi[c] = -h[c].x * sc;
-                    }
-                    if (r < NP) {
-                        put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
-                        if (q >= 2) put_ident8(sm, oBT, NP, r, g);  // for the transpose below
-                    }
+                    if (r < NP) put8(sm, oA, plane, NP, r, g, xr, xi, sig, bad);
                     tmem_st8(R1re + 8 * g, xr);
                     tmem_st8(R1im + 8 * g, xi);
                 }
                 tmem_wait_st();
+                __syncthreads();  // the buffer is consumed: the identity may take its place
+                if (q >= 2 && r < NP)
+                    for (int g = gq; g < nkg; g += XT_GSTRIDE) put_ident8(sm, oBT, NP, r, g);  // for I X
                 xt_sync();
             }
             // X^T (rows into the B^T planes), needed by the Horner steps: the product I X on the tensor
@@ -363,7 +429,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                     mma_commit(&bar);
                 }
                 if (!mma_wait()) { failed = true; break; }
-                for (int g = half; g < nkg; g += 2) {
+                for (int g = gq; g < nkg; g += XT_GSTRIDE) {
                     float dr[8], di[8];
                     ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
                     if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
@@ -376,13 +442,13 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
             auto finish8 = [&](int g, const float (&vr)[8], const float (&vi)[8]) {
                 if (s == 0) {
                     if (r < m) {
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 8; ++c)
                             if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(vr[c], vi[c]);
                     }
                 } else if (sq64) {
                     if (r < m) {
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 8; ++c)
                             if (8 * g + c < m) D0[(size_t)r * m + 8 * g + c] = make_double2(vr[c], vi[c]);
                     }
@@ -403,18 +469,18 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                 {
                     const float fY = ldexpf(1.f, -2 * eX), sigY = ldexpf(1.f, eY), sigS = ldexpf(1.f, eS);
                     const float c1 = s_c[2 * q - 1], c0 = s_c[2 * q - 2];
-                    for (int g = half; g < nkg; g += 2) {
+                    for (int g = gq; g < nkg; g += XT_GSTRIDE) {
                         float dr[8], di[8], xr[8], xi[8];
                         ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
                         ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
                         if (r < NP) {
-    #pragma unroll
+#pragma unroll
                             for (int c = 0; c < 8; ++c) {
                                 dr[c] *= fY;
                                 di[c] *= fY;
                             }
                             put8(sm, oBT, plane, NP, r, g, dr, di, sigY, bad);
-    #pragma unroll
+#pragma unroll
                             for (int c = 0; c < 8; ++c) {
                                 dr[c] = c1 * xr[c] + ((8 * g + c == r && r < m) ? c0 : 0.f);
                                 di[c] = c1 * xi[c];
@@ -433,19 +499,38 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                     if (!mma_wait()) { failed = true; break; }
                     const float f = ldexpf(1.f, -(eS + eY)), sigS = ldexpf(1.f, eS);
                     const float c1 = s_c[2 * j + 1], c0 = s_c[2 * j];
-                    for (int g = half; g < nkg; g += 2) {
-                        float dr[8], di[8], xr[8], xi[8];
-                        ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-                        ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
-    #pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            dr[c] = fmaf(dr[c], f, c1 * xr[c]) + ((8 * g + c == r && r < m) ? c0 : 0.f);
-                            di[c] = fmaf(di[c], f, c1 * xi[c]);
+                    // two column groups per TMEM wait: 8 loads in flight, then the arithmetic
+                    for (int g = gq; g < nkg; g += 2 * XT_GSTRIDE) {
+                        const int gg[2] = {g, g + XT_GSTRIDE};
+                        const bool two = gg[1] < nkg;  // warp-uniform
+                        uint32_t ld[2][4][8];
+                        tmem_ld8_nowait(R0re + 8 * gg[0], ld[0][0]);
+                        tmem_ld8_nowait(R0im + 8 * gg[0], ld[0][1]);
+                        tmem_ld8_nowait(R1re + 8 * gg[0], ld[0][2]);
+                        tmem_ld8_nowait(R1im + 8 * gg[0], ld[0][3]);
+                        if (two) {
+                            tmem_ld8_nowait(R0re + 8 * gg[1], ld[1][0]);
+                            tmem_ld8_nowait(R0im + 8 * gg[1], ld[1][1]);
+                            tmem_ld8_nowait(R1re + 8 * gg[1], ld[1][2]);
+                            tmem_ld8_nowait(R1im + 8 * gg[1], ld[1][3]);
                         }
-                        if (j > 0) {
-                            if (r < NP) put8(sm, oA, plane, NP, r, g, dr, di, sigS, bad);
-                        } else {
-                            finish8(g, dr, di);
+                        tmem_wait_ld();
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            if (h == 1 && !two) break;
+                            float dr[8], di[8];
+#pragma unroll
+                            for (int c = 0; c < 8; ++c) {
+                                const float xr = __uint_as_float(ld[h][2][c]), xi = __uint_as_float(ld[h][3][c]);
+                                dr[c] = fmaf(__uint_as_float(ld[h][0][c]), f, c1 * xr) +
+                                        ((8 * gg[h] + c == r && r < m) ? c0 : 0.f);
+                                di[c] = fmaf(__uint_as_float(ld[h][1][c]), f, c1 * xi);
+                            }
+                            if (j > 0) {
+                                if (r < NP) put8(sm, oA, plane, NP, r, gg[h], dr, di, sigS, bad);
+                            } else {
+                                finish8(gg[h], dr, di);
+                            }
                         }
                     }
                     xt_sync();
@@ -453,10 +538,10 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                 if (failed) break;
             } else {
                 // degree 1: T(X) = I + X
-                for (int g = half; g < nkg; g += 2) {
+                for (int g = gq; g < nkg; g += XT_GSTRIDE) {
                     float xr[8], xi[8];
                     ld_acc8(R1re + 8 * g, R1im + 8 * g, xr, xi);
-    #pragma unroll
+#pragma unroll
                     for (int c = 0; c < 8; ++c) xr[c] += (8 * g + c == r && r < m) ? 1.f : 0.f;
                     finish8(g, xr, xi);
                 }
@@ -472,7 +557,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                     mma_commit(&bar);
                 }
                 if (!mma_wait()) { failed = true; break; }
-                for (int g = half; g < nkg; g += 2) {
+                for (int g = gq; g < nkg; g += XT_GSTRIDE) {
                     float dr[8], di[8];
                     ld_acc8(R1re + 8 * g, R1im + 8 * g, dr, di);
                     if (r < NP) put8(sm, oBT, plane, NP, r, g, dr, di, 1.f, bad);
@@ -488,17 +573,17 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                         mma_commit(&bar);
                     }
                     if (!mma_wait()) { failed = true; break; }
-                    for (int g = half; g < nkg; g += 2) {
+                    for (int g = gq; g < nkg; g += XT_GSTRIDE) {
                         float dr[8], di[8];
                         ld_acc8(R0re + 8 * g, R0im + 8 * g, dr, di);
-    #pragma unroll
+#pragma unroll
                         for (int c = 0; c < 8; ++c) {
                             dr[c] *= f;
                             di[c] *= f;
                         }
                         if (last) {
                             if (r < m) {
-    #pragma unroll
+#pragma unroll
                                 for (int c = 0; c < 8; ++c)
                                     if (8 * g + c < m) Uo[(size_t)r * m + 8 * g + c] = make_float2(dr[c], di[c]);
                             }
@@ -507,7 +592,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                             ld_acc8(R1re + 8 * g, R1im + 8 * g, tr, ti);
                             if (r < NP) {
                                 put8(sm, oA, plane, NP, r, g, dr, di, sigQ, bad);
-    #pragma unroll
+#pragma unroll
                                 for (int c = 0; c < 8; ++c) {
                                     tr[c] *= f;
                                     ti[c] *= f;

@@ -185,7 +185,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
             // per-thread partial sums in the working precision (a thread adds ~m^2/blockDim terms);
             // the cross-thread reduction below is FP64
             T accr[8], acci[8];
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) accr[j] = acci[j] = (T)0;
             __syncthreads();
             for (int r0 = 0; r0 < c; r0 += CG) {
@@ -212,7 +212,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
                         cx<T>* ys[2 * CG];
                         const cx<T>* xs[2 * CG];
                         T sg[2 * CG];
-    #pragma unroll
+#pragma unroll
                         for (int r = 0; r < 2 * CG; ++r) {
                             const int rr = r < cg ? r : 0;
                             xs[r] = V + ((size_t)(q - 1) * CG + rr) * m;
@@ -263,7 +263,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
                             cx<T>* ys[2 * CG];
                             const cx<T>* xs[2 * CG];
                             T sg[2 * CG];
-    #pragma unroll
+#pragma unroll
                             for (int r = 0; r < CG; ++r) {
                                 // v vectors in slots [0, cg), w vectors in [cg, 2cg); unused slots are never read
                                 const int rr = r < cg ? r : 0;
@@ -271,7 +271,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
                                 ys[r] = V + ((size_t)(p + 1) * CG + rr) * m;
                                 sg[r] = (T)1;
                             }
-    #pragma unroll
+#pragma unroll
                             for (int r = 0; r < CG; ++r) {
                                 const int rr = r < cg ? r : 0;
                                 xs[CG + r] = W + (size_t)rr * m;
@@ -296,7 +296,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
                     for (int q = 0; q <= Pt; ++q)
                         for (int r = 0; r < cg; ++r)
                             cfma_conj<T>(Mab, Z[((size_t)q * CG + r) * m + a], V[((size_t)q * CG + r) * m + b]);
-    #pragma unroll
+#pragma unroll
                     for (int j = 0; j < 8; ++j) {
                         if (j < nc) {
                             const cx<T> hc = H[(size_t)(1 + j) * mm + e];
@@ -313,7 +313,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
                 }
             }
             // block reduction of the nc complex sums; then multiply by -i tau / 2^s
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (j >= nc) break;
                 double xr = (double)accr[j], xi = (double)acci[j];

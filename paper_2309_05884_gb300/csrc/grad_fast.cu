@@ -282,7 +282,7 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             const size_t mm = (size_t)m * m;
             const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
             const float tau = (float)B.dt;
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) s_acc[j][threadIdx.x] = f2(0.f, 0.f);
 
             for (int r0 = 0; r0 < c; r0 += GF_CG) {
@@ -291,15 +291,15 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
                 // tile of A (grad_mode 0): rows warp RW + rs + 4 i, columns gf_col(cp, cc); assembled per
                 // copy group, one pass per matrix so that a tile's loads are in flight together
                 float2 At[RPT][CPT];
-    #pragma unroll
+#pragma unroll
                 for (int i = 0; i < RPT; ++i)
-    #pragma unroll
+#pragma unroll
                     for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(0.f, 0.f);
                 if (P.grad_mode == 0) {
-    #pragma unroll
+#pragma unroll
                     for (int i = 0; i < RPT; ++i) {
                         const int a = warp * RW + rs + 4 * i;
-    #pragma unroll
+#pragma unroll
                         for (int cc = 0; cc < CPT; ++cc) {
                             const int b = gf_col(cp, cc);
                             if (a < m && b < m) At[i][cc] = H[(size_t)a * m + b];
@@ -308,10 +308,10 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
                     for (int j = 0; j < nc; ++j) {
                         const float2* Hj = H + (size_t)(1 + j) * mm;
                         const float uj = s_uk[j];
-    #pragma unroll
+#pragma unroll
                         for (int i = 0; i < RPT; ++i) {
                             const int a = warp * RW + rs + 4 * i;
-    #pragma unroll
+#pragma unroll
                             for (int cc = 0; cc < CPT; ++cc) {
                                 const int b = gf_col(cp, cc);
                                 if (a < m && b < m) {
@@ -322,9 +322,9 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
                             }
                         }
                     }
-    #pragma unroll
+#pragma unroll
                     for (int i = 0; i < RPT; ++i)
-    #pragma unroll
+#pragma unroll
                         for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(tau * At[i][cc].y, -tau * At[i][cc].x);  // -i tau h
                 }
                 // v_0 = psi, w_0 = lam of the group's copies (full length, zero tail); Z[0..Pt] = 0
@@ -349,7 +349,7 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             }
             // block reduction of the nc complex sums in FP64 (the per-thread sums cancel strongly when
             // the gradient is small, so they are added without further FP32 rounding); then -i tau
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (j >= nc) break;
                 double xr = (double)s_acc[j][threadIdx.x].x, xi = (double)s_acc[j][threadIdx.x].y;

@@ -239,12 +239,12 @@ grad_rev_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const 
             }
             // GX total = G + GP_1 ;  do_j = -i (tau/2^s) sum_{a,b} GX[a][b] Hc_j[b][a]
             T accr[8], acci[8];
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) accr[j] = acci[j] = (T)0;
             for (size_t e = threadIdx.x; e < mm; e += blockDim.x) {
                 const int a = (int)(e / m), b = (int)(e - (size_t)a * m);
                 const cx<T> gx = cadd<T>(G[e], GP(1)[e]);
-    #pragma unroll
+#pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j < nc) {
                         const cx<T> hc = H[(size_t)(1 + j) * mm + (size_t)b * m + a];
@@ -253,7 +253,7 @@ grad_rev_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const 
                     }
                 }
             }
-    #pragma unroll
+#pragma unroll
             for (int j = 0; j < 8; ++j) {
                 if (j >= nc) break;
                 double xr = (double)accr[j], xi = (double)acci[j];
