@@ -187,12 +187,84 @@ __device__ __forceinline__ void gf_group(const GfSmem& S, const float2 (&At)[GfS
     }
 }
 
+// One (slice, block) item with tile size MT: for every copy group, the A tile, the chains, the M
+// tile and the contraction; each thread's contraction terms accumulate in s_acc.
 template <int MT>
-__global__ void __launch_bounds__(GF_THREADS, 1)
-grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, const float2* __restrict__ psi_st,
-                 const float2* __restrict__ lam_st, double2* __restrict__ partial, int m_lo) {
+__device__ __forceinline__ void gf_item(const GfSmem& S, const DevPlan& P, const DevBlock& B, int m, int c, int kw,
+                                        int Pt, const float2* H, size_t mm, float tau, const float* s_uk,
+                                        const float* s_if, int nc, const float2* __restrict__ psi_st,
+                                        const float2* __restrict__ lam_st, float2 (*s_acc)[GF_THREADS]) {
     using Sh = GfShape<MT>;
     constexpr int RPT = Sh::RPT, CPT = Sh::CPT, RW = Sh::RW;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int cp = lane & 7, rs = lane >> 3;
+    for (int r0 = 0; r0 < c; r0 += GF_CG) {
+        const int cg = (c - r0) < GF_CG ? (c - r0) : GF_CG;
+        const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
+        // tile of A (grad_mode 0): rows warp RW + rs + 4 i, columns gf_col(cp, cc); assembled per
+        // copy group, one pass per matrix so that a tile's loads are in flight together
+        float2 At[RPT][CPT];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(0.f, 0.f);
+        if (P.grad_mode == 0) {
+#pragma unroll
+            for (int i = 0; i < RPT; ++i) {
+                const int a = warp * RW + rs + 4 * i;
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) {
+                    const int b = gf_col(cp, cc);
+                    if (a < m && b < m) At[i][cc] = H[(size_t)a * m + b];
+                }
+            }
+            for (int j = 0; j < nc; ++j) {
+                const float2* Hj = H + (size_t)(1 + j) * mm;
+                const float uj = s_uk[j];
+#pragma unroll
+                for (int i = 0; i < RPT; ++i) {
+                    const int a = warp * RW + rs + 4 * i;
+#pragma unroll
+                    for (int cc = 0; cc < CPT; ++cc) {
+                        const int b = gf_col(cp, cc);
+                        if (a < m && b < m) {
+                            const float2 hc = Hj[(size_t)a * m + b];
+                            At[i][cc].x = fmaf(uj, hc.x, At[i][cc].x);
+                            At[i][cc].y = fmaf(uj, hc.y, At[i][cc].y);
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < RPT; ++i)
+#pragma unroll
+                for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(tau * At[i][cc].y, -tau * At[i][cc].x);  // -i tau h
+        }
+        // v_0 = psi, w_0 = lam of the group's copies (full length, zero tail); Z[0..Pt] = 0
+        for (int e = threadIdx.x; e < GF_CG * GF_VL; e += GF_THREADS) {
+            const int r = e / GF_VL, a = e % GF_VL;
+            const bool in = r < cg && a < m;
+            S.x(0, r)[a] = in ? psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a] : f2(0.f, 0.f);
+            S.x(0, GF_CG + r)[a] = in ? lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a]
+                                      : f2(0.f, 0.f);
+        }
+        for (int e = threadIdx.x; e < (Pt + 1) * GF_CG * GF_VL; e += GF_THREADS) S.Z[e] = f2(0.f, 0.f);
+        __syncthreads();
+        if (cg == 2) {
+            gf_group<MT, 4>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
+        } else {
+            // one copy: the w vectors live in slot CG = 1 of the NV = 2 layout; move w_0 there
+            for (int e = threadIdx.x; e < GF_VL; e += GF_THREADS) S.x(0, 1)[e] = S.x(0, GF_CG)[e];
+            __syncthreads();
+            gf_group<MT, 2>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
+        }
+        __syncthreads();  // X, Z are refilled by the next copy group
+    }
+}
+
+__global__ void __launch_bounds__(GF_THREADS, 1)
+grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, const float2* __restrict__ psi_st,
+                 const float2* __restrict__ lam_st, double2* __restrict__ partial) {
     extern __shared__ __align__(16) unsigned char dsm[];
     GfSmem S;
     S.X = reinterpret_cast<float2*>(dsm);
@@ -205,7 +277,6 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
     __shared__ float2 s_acc[8][GF_THREADS];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int cp = lane & 7, rs = lane >> 3;
     const int nc = P.nc;
     if (threadIdx.x == 0) {
         double f = 1.0;
@@ -223,7 +294,10 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
     __shared__ int s_list[GF_THREADS];
     __shared__ int s_nl;
     __shared__ int s_wc[32];
-    // slices this launch owns: blocks of size (m_lo, MT], slices that need no sub-slicing
+    // slices this launch owns: blocks of up to 128 states, slices that need no sub-slicing; the norm
+    // bound and pulses of each tested slice are kept for the setup below
+    __shared__ double s_beta[GF_THREADS];
+    __shared__ float s_ul[GF_THREADS][8];
     auto want = [&](long long it) -> bool {
         int bi;
         long long k;
@@ -236,8 +310,14 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             k = P.k0 + it % NK;
         }
         const DevBlock& Bw = P.blocks[bi];
-        if (Bw.m <= m_lo || Bw.m > MT) return false;
-        return P.grad_mode != 0 || slice_halvings(slice_beta(P, Bw, u, k), theta, GF_SUB_MAX) == 0;
+        if (Bw.m > 128) return false;
+        const double beta = slice_beta(P, Bw, u, k);
+        for (int j = 0; j < nc; ++j) {
+            const double x = u[(size_t)(Bw.u_row + k) * nc + j];
+            s_ul[threadIdx.x][j] = isfinite(x) ? (float)x : 0.f;
+        }
+        s_beta[threadIdx.x] = beta;
+        return P.grad_mode != 0 || slice_halvings(beta, theta, GF_SUB_MAX) == 0;
     };
     for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
         const int nl = s_nl;
@@ -258,14 +338,9 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             const int m = B.m, c = B.c;
             __syncthreads();  // the previous item's readers of s_* are done
             if (threadIdx.x == 0) {
-                double beta = B.h0_norm1;
-                for (int j = 0; j < nc; ++j) {
-                    const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
-                    const double x = isfinite(uk) ? uk : 0.0;
-                    s_uk[j] = (float)x;
-                    beta += fabs(x) * B.hc_norm1[j];
-                }
-                beta *= B.dt;
+                const int ti = s_list[li];  // the thread that tested this slice
+                for (int j = 0; j < nc; ++j) s_uk[j] = s_ul[ti][j];
+                double beta = s_beta[ti];
                 int Pt = 0, sub = 0;
                 if (P.grad_mode == 0) {
                     while (beta > theta && sub < GF_SUB_MAX) { beta *= 0.5; ++sub; }
@@ -285,68 +360,10 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
 #pragma unroll
             for (int j = 0; j < 8; ++j) s_acc[j][threadIdx.x] = f2(0.f, 0.f);
 
-            for (int r0 = 0; r0 < c; r0 += GF_CG) {
-                const int cg = (c - r0) < GF_CG ? (c - r0) : GF_CG;
-                const long long kpsi = P.grad_mode == 0 ? kw : kw + 1;
-                // tile of A (grad_mode 0): rows warp RW + rs + 4 i, columns gf_col(cp, cc); assembled per
-                // copy group, one pass per matrix so that a tile's loads are in flight together
-                float2 At[RPT][CPT];
-#pragma unroll
-                for (int i = 0; i < RPT; ++i)
-#pragma unroll
-                    for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(0.f, 0.f);
-                if (P.grad_mode == 0) {
-#pragma unroll
-                    for (int i = 0; i < RPT; ++i) {
-                        const int a = warp * RW + rs + 4 * i;
-#pragma unroll
-                        for (int cc = 0; cc < CPT; ++cc) {
-                            const int b = gf_col(cp, cc);
-                            if (a < m && b < m) At[i][cc] = H[(size_t)a * m + b];
-                        }
-                    }
-                    for (int j = 0; j < nc; ++j) {
-                        const float2* Hj = H + (size_t)(1 + j) * mm;
-                        const float uj = s_uk[j];
-#pragma unroll
-                        for (int i = 0; i < RPT; ++i) {
-                            const int a = warp * RW + rs + 4 * i;
-#pragma unroll
-                            for (int cc = 0; cc < CPT; ++cc) {
-                                const int b = gf_col(cp, cc);
-                                if (a < m && b < m) {
-                                    const float2 hc = Hj[(size_t)a * m + b];
-                                    At[i][cc].x = fmaf(uj, hc.x, At[i][cc].x);
-                                    At[i][cc].y = fmaf(uj, hc.y, At[i][cc].y);
-                                }
-                            }
-                        }
-                    }
-#pragma unroll
-                    for (int i = 0; i < RPT; ++i)
-#pragma unroll
-                        for (int cc = 0; cc < CPT; ++cc) At[i][cc] = f2(tau * At[i][cc].y, -tau * At[i][cc].x);  // -i tau h
-                }
-                // v_0 = psi, w_0 = lam of the group's copies (full length, zero tail); Z[0..Pt] = 0
-                for (int e = threadIdx.x; e < GF_CG * GF_VL; e += GF_THREADS) {
-                    const int r = e / GF_VL, a = e % GF_VL;
-                    const bool in = r < cg && a < m;
-                    S.x(0, r)[a] = in ? psi_st[B.s_off + kpsi * c * m + (size_t)(r0 + r) * m + a] : f2(0.f, 0.f);
-                    S.x(0, GF_CG + r)[a] = in ? lam_st[B.s_off + (long long)(kw + 1) * c * m + (size_t)(r0 + r) * m + a]
-                                              : f2(0.f, 0.f);
-                }
-                for (int e = threadIdx.x; e < (Pt + 1) * GF_CG * GF_VL; e += GF_THREADS) S.Z[e] = f2(0.f, 0.f);
-                __syncthreads();
-                if (cg == 2) {
-                    gf_group<MT, 4>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
-                } else {
-                    // one copy: the w vectors live in slot CG = 1 of the NV = 2 layout; move w_0 there
-                    for (int e = threadIdx.x; e < GF_VL; e += GF_THREADS) S.x(0, 1)[e] = S.x(0, GF_CG)[e];
-                    __syncthreads();
-                    gf_group<MT, 2>(S, At, m, Pt, s_if, H, mm, nc, s_acc);
-                }
-                __syncthreads();  // X, Z are refilled by the next copy group
-            }
+            if (m <= 64)
+                gf_item<64>(S, P, B, m, c, kw, Pt, H, mm, tau, s_uk, s_if, nc, psi_st, lam_st, s_acc);
+            else
+                gf_item<128>(S, P, B, m, c, kw, Pt, H, mm, tau, s_uk, s_if, nc, psi_st, lam_st, s_acc);
             // block reduction of the nc complex sums in FP64 (the per-thread sums cancel strongly when
             // the gradient is small, so they are added without further FP32 rounding); then -i tau
 #pragma unroll
@@ -376,26 +393,9 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             }
         }
     }
-    (void)cp;
-    (void)rs;
 }
 
-template <int MT>
-size_t gf_smem() {
-    return (size_t)(GF_PM + 1) * (GF_NVM + GF_CG) * GF_VL * sizeof(float2);
-}
-
-template <int MT>
-int launch_one(const DevPlan& P, const double* u, const void* psi, const void* lam, double2* partial, int m_lo,
-               int grid, cudaStream_t st) {
-    const size_t sm = gf_smem<MT>();
-    if (cudaFuncSetAttribute(grad_fast_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) !=
-        cudaSuccess)
-        return -1;
-    grad_fast_kernel<MT><<<grid, GF_THREADS, sm, st>>>(P, 1e-9, 3.0, u, (const float2*)psi, (const float2*)lam,
-                                                        partial, m_lo);
-    return cudaGetLastError() == cudaSuccess ? 0 : -1;
-}
+size_t gf_smem() { return (size_t)(GF_PM + 1) * (GF_NVM + GF_CG) * GF_VL * sizeof(float2); }
 
 }  // namespace
 
@@ -403,11 +403,13 @@ int grad_fast_max_m(int prec) { return prec == QOC_PREC_F64 ? 0 : 128; }
 
 int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
                      int max_m, int grid, cudaStream_t st) {
-    if (P.prec == QOC_PREC_F64 || P.nc > 8) return 0;
-    int rc = 0;
-    if (max_m > 0) rc |= launch_one<64>(P, u, psi_store, lam_store, partial, 0, grid, st);
-    if (max_m > 64) rc |= launch_one<128>(P, u, psi_store, lam_store, partial, 64, grid, st);
-    return rc;
+    if (P.prec == QOC_PREC_F64 || P.nc > 8 || max_m < 1) return 0;
+    const size_t sm = gf_smem();
+    if (cudaFuncSetAttribute(grad_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
+        return -1;
+    grad_fast_kernel<<<grid, GF_THREADS, sm, st>>>(P, 1e-9, 3.0, u, (const float2*)psi_store, (const float2*)lam_store,
+                                                   partial);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 }  // namespace qoc

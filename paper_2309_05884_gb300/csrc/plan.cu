@@ -795,8 +795,8 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     const int nrev = (int)p->classes.size();  // reverse-mode derivative launches: one per class
     int ncls = 0;                               // exponential launches
     for (const auto& c : p->classes) ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
-    // register-tile derivative launches per gradient pass (FP32 plans): one per size range used
-    const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? (p->max_m > 64 ? 2 : 1) : 0;
+    // register-tile derivative launch per gradient pass (FP32 plans)
+    const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
     if (p->nseg == 1)
         *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + nrev + 1 : 1 + ncls + 1 + 1;
     else
