@@ -488,7 +488,7 @@ int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_stor
     } else {
         const size_t sm = grad_smem<float>(max_m);
         cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-9, 3.0, u, (const float2*)psi_store,
+        grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, GF32_SERIES_TOL, 3.0, u, (const float2*)psi_store,
                                                           (const float2*)lam_store, partial, scratch, slot_bytes,
                                                           grad_mode_of<float>(max_m), max_m, grad_fast_max_m(P.prec));
     }

@@ -407,7 +407,7 @@ int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, c
     const size_t sm = gf_smem();
     if (cudaFuncSetAttribute(grad_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return -1;
-    grad_fast_kernel<<<grid, GF_THREADS, sm, st>>>(P, 1e-9, 3.0, u, (const float2*)psi_store, (const float2*)lam_store,
+    grad_fast_kernel<<<grid, GF_THREADS, sm, st>>>(P, GF32_SERIES_TOL, 3.0, u, (const float2*)psi_store, (const float2*)lam_store,
                                                    partial);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

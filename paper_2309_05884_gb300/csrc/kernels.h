@@ -10,6 +10,10 @@ namespace qoc {
 
 // Degree table of the Taylor / Paterson-Stockmeyer scheme: theta[i] is the largest 1-norm bound
 // for which degree (p_i q_i) keeps the truncation below the working unit roundoff.
+// FP32 exact-derivative series: terms below 2^-27 (about an eighth of the FP32 unit roundoff,
+// relative to the leading term) are dropped
+constexpr double GF32_SERIES_TOL = 7.450580596923828e-09;
+
 struct ExpmTables {
     double theta[9];
     int n_deg;          // degrees allowed (prefix of the table)

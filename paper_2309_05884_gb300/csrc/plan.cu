@@ -596,7 +596,10 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     const int degs[9] = {2, 4, 6, 9, 12, 16, 20, 25, 30};
     const double unit = o.prec == QOC_PREC_F64 ? std::ldexp(1.0, -53) : std::ldexp(1.0, -24);
     for (int i = 0; i < 9; ++i) p->tabs.theta[i] = theta_for(degs[i], unit);
-    for (int q = 1; q <= 16; ++q) p->tabs.theta_odd[q - 1] = theta_for(2 * q - 1, unit);
+    // tensor-core degrees: its products round at about 2^-23 (two FP16 halves, FP32 accumulation), so
+    // the truncation bound is matched to that rather than to FP32's 2^-24
+    const double tc_unit = o.prec == QOC_PREC_F64 ? unit : std::ldexp(1.0, -23);
+    for (int q = 1; q <= 16; ++q) p->tabs.theta_odd[q - 1] = theta_for(2 * q - 1, tc_unit);
     if (o.prec == QOC_PREC_F64) {
         p->tabs.n_deg = 9;
         p->tabs.theta_cap = p->tabs.theta[8];
