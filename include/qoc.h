@@ -251,10 +251,13 @@ int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
  * by size); kind 1 = warp-packed kernel (m <= 32 FP32, <= 16 FP64, not with QOC_PREC_F32), param =
  * matrices per warp (0 = as many as fit); kind 2 = tcgen05 tensor-core kernel (FP32 plans, m <= 112;
  * products as in qoc_tc_cgemm), param 0 = only the slices that need no squaring (the block's other
- * slices run on the tiled kernel in a second launch), param 1 = every slice.  Blocks no rule covers
+ * slices run on the tiled kernel in a second launch), param 1 = every slice; kind 3 = tcgen05 tiled
+ * batched GEMMs for large blocks (FP32 plans, m <= 2048; 128 x 128 output tiles, one launch per
+ * product over a chunk of slices) for the slices that need no squaring, the tiled kernel for the
+ * rest (param ignored).  Blocks no rule covers
  * use the tiled kernel.  At plan creation QOC_PREC_F32 plans use kind 2, param 0 for blocks of
- * 25..112 states and the tiled kernel for the rest; QOC_PREC_F32_ALL and FP64 plans use the tiled
- * kernel.  A tensor-core product
+ * 25..112 states, kind 3 for 113..2048 and the tiled kernel for the rest; QOC_PREC_F32_ALL and FP64
+ * plans use the tiled kernel.  A tensor-core product
  * (two FP16 halves per operand, all four split products) errs up to about 2x an FP32 one, which
  * the squarings of large-norm slices would amplify.   The plan's
  * workspace size may change: query qoc_plan_workspace_bytes again.  An autotuner times candidate

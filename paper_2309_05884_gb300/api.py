@@ -286,7 +286,9 @@ class Plan:
 
     def set_expm_rules(self, rules) -> None:
         """rules: [(m_max, kind, param)], kind 0 = tiled CTA kernel (param R), 1 = warp-packed (param =
-        matrices per warp).  Reallocates the workspace if its size changes."""
+        matrices per warp), 2 = tensor cores, one CTA per slice (m <= 112; param 0: slices without
+        squarings, 1: all), 3 = tiled tensor-core GEMMs (m <= 2048, slices without squarings).
+        Reallocates the workspace if its size changes."""
         n = len(rules)
         mx = (C.c_int * n)(*[r[0] for r in rules])
         kd = (C.c_int * n)(*[r[1] for r in rules])

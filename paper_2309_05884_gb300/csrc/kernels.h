@@ -42,6 +42,13 @@ int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, 
                      const int2* items, long long n_items, int MP, int per_warp, void* Uout, int grid,
                      cudaStream_t st);
 
+// ---- expm_large.cu (tcgen05 tiled GEMMs for blocks of up to 2048 states, slices without squaring)
+int expm_large_supported(int prec, int m);
+size_t expm_large_scratch_bytes(int m_max, long long max_items);
+int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
+                      const int2* items, long long n_items, void* Uout, char* scratch, int m_max, cudaStream_t st);
+long long expm_large_launches(const ExpmTables& tabs, int m_max, long long total);
+
 // ---- grad_fast.cu (exact slice derivatives, FP32, m <= 128, unsplit slices; A in registers)
 int grad_fast_max_m(int prec);
 int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,

@@ -37,7 +37,7 @@ struct ExpmClass {
 // Kernel choice for blocks of size <= m_max (rules sorted by m_max; the first match wins).
 struct ExpmRule {
     int m_max;
-    int kind;   // 0 CTA tiles, 1 warp-packed
+    int kind;   // 0 CTA tiles, 1 warp-packed, 2 tensor cores (m <= 112), 3 tiled tensor-core GEMMs
     int param;  // R (CTA) or matrices per warp (warp-packed; 0 = as many as fit)
 };
 
@@ -190,7 +190,13 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
         if (c.kind == 1)
             rc = launch_expm_warp(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                   c.R, c.per_warp, ws + p->off_U, c.grid, st);
-        else if (c.kind == 2) {
+        else if (c.kind == 3) {
+            rc = launch_expm_large(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                   ws + p->off_U, ws + p->off_expm, c.m_max, st);
+            if (rc == 0)
+                rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
+                                 c.R2, ws + p->off_U, ws + p->off_expm, c.slot2, c.m_max, c.grid2, st, 1);
+        } else if (c.kind == 2) {
             rc = launch_expm_tc(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                 ws + p->off_U, ws + p->off_expm, c.slot_bytes, c.m_max, c.grid, st, c.R);
             if (rc == 0 && c.R == 0)
@@ -282,6 +288,9 @@ int build_classes(qoc_plan* p) {
             } else if (r.kind == 2) {
                 if (!expm_tc_supported(wp, m)) continue;
                 key = {2, r.param > 0 ? 1 : 0, 0};
+            } else if (r.kind == 3) {
+                if (!expm_large_supported(wp, m)) continue;
+                key = {3, 0, 0};
             } else {
                 const int rmax = wp == QOC_PREC_F64 ? 4 : 7;
                 key = {0, r.param > 0 ? std::min(r.param, rmax) : expm_r_for(wp == QOC_PREC_F64 ? 0 : 1, m), 0};
@@ -327,6 +336,15 @@ int build_classes(qoc_plan* p) {
                 c.slot2 = align_up(expm_slot_bytes(1, c.m_max), 256);
                 p->expm_scratch = std::max(p->expm_scratch, c.slot2 * (size_t)c.grid2);
             }
+        } else if (c.kind == 3) {
+            // tiled tensor-core GEMMs for the slices without squarings, the CUDA-core tiles for the rest
+            c.grid = 1;
+            c.slot_bytes = align_up(expm_large_scratch_bytes(c.m_max, max_items), 256);
+            p->expm_scratch = std::max(p->expm_scratch, c.slot_bytes);
+            c.R2 = expm_r_for(1, c.m_max);
+            c.grid2 = (int)std::max<long long>(1, std::min<long long>(max_items, expm_grid_limit(1, c.R2)));
+            c.slot2 = align_up(expm_slot_bytes(1, c.m_max), 256);
+            p->expm_scratch = std::max(p->expm_scratch, c.slot2 * (size_t)c.grid2);
         } else if (c.kind == 1) {
             const long long groups = (max_items + c.per_warp - 1) / c.per_warp;
             const long long ctas = (groups + (c.R == 32 ? 2 : 4) - 1) / (c.R == 32 ? 2 : 4);
@@ -609,14 +627,16 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     }
     p->tabs.sq_f64 = o.prec == QOC_PREC_F32_ALL ? 0 : 1;
 
-    // expm size classes.  In plans with the FP64 squaring chain the slices of blocks with 25..112
-    // states that need no squaring go to the tensor cores; a tensor-core product errs up to about 2x
+    // expm size classes.  In plans with the FP64 squaring chain the slices of blocks with 25..2048
+    // states that need no squaring go to the tensor cores (one CTA per slice up to 112 states, tiled
+    // GEMMs beyond); a tensor-core product errs up to about 2x
     // an FP32 one, so slices whose squarings would amplify that stay on the tiled CUDA-core kernels,
     // as do all other blocks.  All-FP32 plans (typically large norms, where most slices are squared)
     // keep the tiled kernels; the autotuner may pick warp-packed or tensor-core rules.
     if (o.prec == QOC_PREC_F32) {
         p->rules.push_back({24, 0, 0});
         p->rules.push_back({112, 2, 0});
+        p->rules.push_back({2048, 3, 0});  // larger blocks: tiled tensor-core GEMMs
     }
     p->rules.push_back({1 << 30, 0, 0});
     {
@@ -796,8 +816,15 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     // gathers, one expm launch per size class, sweeps, overlap, slice derivatives, reduction
     // (+ the iteration counter when optimising); propagate: gather, expm, sweep, memset, store
     const int nrev = (int)p->classes.size();  // reverse-mode derivative launches: one per class
-    int ncls = 0;                               // exponential launches
-    for (const auto& c : p->classes) ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
+    int ncls = 0;                               // exponential launches per pass over all slices
+    for (const auto& c : p->classes) {
+        if (c.kind == 3) {
+            const long long per = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
+            ncls += (int)expm_large_launches(p->tabs, c.m_max, per) + 1;
+        } else {
+            ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
+        }
+    }
     // register-tile derivative launch per gradient pass (FP32 plans)
     const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
     if (p->nseg == 1)
@@ -831,8 +858,9 @@ int qoc_plan_set_expm_rules(qoc_plan* p, int n_rules, const int* m_max, const in
     if (!p || n_rules < 1 || !m_max || !kind || !param) return set_error(QOC_EINVAL, "null argument or no rule");
     std::vector<ExpmRule> rules;
     for (int i = 0; i < n_rules; ++i) {
-        if (kind[i] < 0 || kind[i] > 2)
-            return set_error(QOC_EINVAL, "rule kind must be 0 (CTA tiles), 1 (warp-packed) or 2 (tensor cores)");
+        if (kind[i] < 0 || kind[i] > 3)
+            return set_error(QOC_EINVAL,
+                             "rule kind must be 0 (CTA tiles), 1 (warp-packed), 2 (tensor cores) or 3 (tiled tensor cores)");
         if (param[i] < 0) return set_error(QOC_EINVAL, "rule parameter must be >= 0");
         if (kind[i] == 2 && param[i] > 1)
             return set_error(QOC_EINVAL, "tensor-core rule parameter must be 0 (unsquared slices) or 1 (all)");

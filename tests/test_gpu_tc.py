@@ -175,3 +175,63 @@ def test_tensor_core_expm_in_checkpoint_windows():
         res.append((o.cpu().numpy(), g.cpu().numpy()))
     assert abs(res[0][0][0] - res[1][0][0]) <= 1e-12
     assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * max(1.0, np.abs(res[0][1]).max())
+
+
+def test_large_block_tensor_core_propagators_match_oracle():
+    # D_12 blocks of 128..346 states (two or three 128-row tiles, ragged tails), tau = 0.02: the tiled
+    # tensor-core GEMMs (rule kind 3) against the FP64 oracle and the CUDA-core tiles
+    from oracle import grape as gr
+    from paper_2309_05884_gb300 import api
+    from paper_2309_05884_gb300 import inputs as I
+    s = I.xxz_ring(12, 0.12, 6)
+    B = api.Basis(s)
+    u = I.pulses_normal(29, s.N, 3)
+    plan = api.Plan(B, s.N, s.tau, prec="f32")
+    ut = torch.from_numpy(u).to(DEV)
+    plan.set_expm_rules([(1 << 30, 0, 0)])
+    U_t = plan.expm(ut).cpu().numpy()
+    plan.set_expm_rules([(2048, 3, 0)])
+    assert all(c[0] == 3 for c in plan.expm_classes())
+    U_c = plan.expm(ut).cpu().numpy()
+    torch.cuda.synchronize()
+    plan.sync_status()
+    off, e_c, e_t = 0, 0.0, 0.0
+    for b in plan.active_blocks():
+        m = B.blocks[b][1]
+        h0, hc = B.block_matrices(b)
+        Uref = gr.propagators(dict(h0=h0, hc=list(hc)), u, s.tau)
+        n = s.N * m * m
+        e_c = max(e_c, np.abs(U_c[off:off + n].reshape(s.N, m, m) - Uref).max())
+        e_t = max(e_t, np.abs(U_t[off:off + n].reshape(s.N, m, m) - Uref).max())
+        off += n
+    assert e_c <= 2e-5, (e_c, e_t)
+    assert e_c <= max(8 * e_t, 5e-6), (e_c, e_t)
+
+
+@pytest.mark.slow
+def test_large_block_tensor_core_gradient_d14_first_block():
+    # D_14 A1 (687 states), checkpointed FP32 gradient with the tiled tensor-core expm against the
+    # same plan on the CUDA-core tiles (the CUDA-core path itself is checked against the oracle in
+    # test_gpu_checkpoint)
+    from paper_2309_05884_gb300 import api
+    from paper_2309_05884_gb300 import inputs as I
+    s = I.xxz_ring(14, 4.0, 200)
+    B = api.Basis(s, first_block_only=True)
+    x = I.random_state(203, 2 ** 14)
+    blk = B.state_to_blocks(x)
+    blk[687:] = 0
+    blk /= np.linalg.norm(blk)
+    b0 = B.state_to_blocks(I.basis_state(14, 0))
+    u = torch.from_numpy(I.pulses_normal(2, s.N, 3)).to(DEV)
+    d0, df = api.to_device(b0, DEV), api.to_device(blk, DEV)
+    res = []
+    for rules in ([(1 << 30, 0, 0)], [(2048, 3, 0)]):
+        plan = api.Plan(B, s.N, s.tau, prec="f32", ckpt_segment=-1)
+        plan.set_expm_rules(rules)
+        o, g = plan.fidelity_and_grad(u, d0, df)
+        torch.cuda.synchronize()
+        plan.sync_status()
+        res.append((o.cpu().numpy(), g.cpu().numpy()))
+    (o_t, g_t), (o_c, g_c) = res
+    assert abs(o_c[0] - o_t[0]) <= 1e-5
+    assert np.linalg.norm(g_c - g_t) / np.linalg.norm(g_t) <= 1e-5
