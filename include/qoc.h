@@ -235,10 +235,11 @@ int qoc_optimize_pulses(qoc_plan* plan, double* u, const double* psi0, const dou
 
 /* ---------------------------------------------------------------- tuning */
 /* Sweep kernel of the forward/backward passes (Sec. II.A, Eq. exppropagator; costates through
- * U_k^dagger as in Appendix B).  cl = 2, 4 or 8 splits each (direction, block) chain over a
- * thread-block cluster of cl CTAs (rows of U_k per CTA, state exchanged through distributed shared
- * memory each step); 0 runs one CTA per chain; -1 restores the automatic choice made at plan
- * creation (clusters when every chain's cluster can be resident at once and blocks have m >= 24).
+ * U_k^dagger as in Appendix B).  cl = 2..8 splits each (direction, block) chain over a
+ * thread-block cluster of cl CTAs (rows of U_k per CTA, streamed through shared memory in sub-blocks
+ * when they do not fit at once; state exchanged through distributed shared memory each step); 0 runs
+ * one CTA per chain; -1 restores the automatic choice made at plan creation (the largest cluster,
+ * 8 down to 2, for which every chain's cluster can be resident at once; blocks of m >= 24).
  * Returns QOC_EINVAL for other values, QOC_EUNSUPPORTED if the cluster buffers of the plan's largest
  * block do not fit in shared memory.  The paper has no counterpart: it is a launch-shape choice. */
 int qoc_plan_set_sweep_cluster(qoc_plan* plan, int cl);

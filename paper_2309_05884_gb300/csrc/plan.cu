@@ -841,7 +841,7 @@ int qoc_plan_set_sweep_cluster(qoc_plan* p, int cl) {
         p->sweep_cl = sweep_cluster_size(p->opts.prec, p->nb, p->max_m, p->max_c);
         return QOC_OK;
     }
-    if (cl != 0 && cl != 2 && cl != 4 && cl != 8) return set_error(QOC_EINVAL, "cluster size must be -1, 0, 2, 4 or 8");
+    if (cl != 0 && (cl < 2 || cl > 8)) return set_error(QOC_EINVAL, "cluster size must be -1, 0 or 2..8");
     if (cl > 0 && !sweep_cluster_fits(p->opts.prec, p->max_m, p->max_c, cl))
         return set_error(QOC_EUNSUPPORTED, "cluster sweep buffers do not fit in shared memory");
     p->sweep_cl = cl;

@@ -4,7 +4,8 @@
 // A sweep is N dependent matrix-vector products; with one CTA per chain (sweep.cu) a step is bounded
 // by that CTA's fetch of the whole U_k.  Here a cluster of CL CTAs walks one (direction, block) chain:
 // CTA q owns rows [q R, q R + R) of every U_k (R = ceil(m / CL)) and streams them through an
-// STAGES-deep cp.async pipeline, so each SM moves only R m elements per step, far ahead of use.
+// STAGES-slot cp.async ring, so each SM moves only R m elements per step, far ahead of use; when R
+// rows do not fit a slot (large blocks) the ring carries sub-blocks of RS rows.
 //   forward  psi_k = U_k psi_{k-1}: a CTA computes its rows of psi_k into its exchange buffer; after
 //            the cluster barrier every CTA gathers the whole vector from its peers' buffers (DSMEM);
 //   backward lam_{k-1} = U_k^dagger lam_k: a CTA forms the partial sums over its rows for every
@@ -13,6 +14,8 @@
 // before the peers' reads and those reads before the buffer is written again two steps later.  The
 // barrier and the cp.async waits are hardware waits: every CTA of a cluster runs the same number of
 // steps, and the cluster launch makes its CTAs co-resident.
+#include <algorithm>
+
 #include "../../include/qoc.h"
 #include "kernels.h"
 #include "tma.cuh"
@@ -58,14 +61,17 @@ __device__ __forceinline__ void cp_wait() {
     asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-// Dynamic shared memory: U stages [STAGES][R][m], x [c][m] (this CTA's input: the whole vector
-// forward, its own rows backward), exchange buffers xb[2][c][m].
-template <class T, int STAGES>
+// Dynamic shared memory: U ring [STAGES][RS][m], x [c][m] (this CTA's input: the whole vector
+// forward, its own rows backward), exchange buffers xb[2][c][m].  SUB = false: a slot holds all of a
+// CTA's rows (RS >= R); SUB = true: the rows of a step pass through the ring in sub-blocks of RS.
+template <class T, int STAGES, bool SUB>
 __global__ void __launch_bounds__(SC_THREADS)
 sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __restrict__ fwd_init,
                      cx<T>* __restrict__ fwd_out, const cx<T>* __restrict__ bwd_init, cx<T>* __restrict__ bwd_out,
-                     cx<T>* __restrict__ psi_st, cx<T>* __restrict__ lam_st, int dirs, int CL, int max_m, int max_c) {
+                     cx<T>* __restrict__ psi_st, cx<T>* __restrict__ lam_st, int dirs, int CL, int max_m, int max_c,
+                     int RS) {
     extern __shared__ __align__(16) unsigned char dsm[];
+    __shared__ cx<T> red[SC_THREADS / 32];
     const int chain = (int)(blockIdx.x / (unsigned)CL);
     const int q = (int)cluster_rank();
     const int nfw = (dirs & 1) ? P.nb : 0;
@@ -76,9 +82,8 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
     const long long mmp = B.mmp;
     const int R = (m + CL - 1) / CL;
     const int r0 = min(m, q * R), r1 = min(m, r0 + R), nr = r1 - r0;  // nr may be 0
-    const int Rmax = (max_m + CL - 1) / CL;
-    cx<T>* ust = reinterpret_cast<cx<T>*>(dsm);                  // [STAGES][Rmax * max_m]
-    cx<T>* x = ust + (size_t)STAGES * Rmax * max_m;               // [max_c][max_m]
+    cx<T>* ust = reinterpret_cast<cx<T>*>(dsm);                  // [STAGES][RS * max_m]
+    cx<T>* x = ust + (size_t)STAGES * RS * max_m;                 // [max_c][max_m]
     cx<T>* xb = x + (size_t)max_c * max_m;                        // [2][max_c][max_m]
     const size_t xbs = (size_t)max_c * max_m;
     const int tid = threadIdx.x;
@@ -95,40 +100,51 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
             if (o >= r0 && o < r1) st[s0 + kst * c * m + e] = init[e];
         }
     }
-    // prologue of the U pipeline: steps 0 .. STAGES-2
-    auto issue = [&](int t) {
-        if (t < NK && nr > 0) {
-            const int i = fwd ? t : NK - 1 - t;
-            const cx<T>* src = U + B.u_off + (long long)i * mmp + (long long)r0 * m;
-            cx<T>* dst = ust + (size_t)(t % STAGES) * Rmax * max_m;
-            for (int e = tid; e < nr * m; e += SC_THREADS) cp_async(dst + e, src + e);
-        }
-        cp_commit();
+    // Work split of one pass over staged rows ra .. ra + rn of this CTA's rows of U_i: forward outputs
+    // (those rows x copies), backward outputs (all m x copies), 2^lg threads each, nout <= SC_THREADS
+    // >> lg; long forward rows (m >= 512, sub-block mode) may span several warps.
+    const int lg_max = SUB && fwd && m >= 512 ? 8 : 5;
+    auto split = [&](int nout) {
+        int lg = 0;
+        while (lg < lg_max && (2 << lg) * nout <= SC_THREADS) ++lg;
+        return lg;
     };
-    for (int t = 0; t < STAGES - 1; ++t) issue(t);
-    __syncthreads();
-
-    // work split: forward outputs (own rows x copies), G threads each; backward outputs (all m x copies)
-    const int nout = fwd ? nr * c : m * c;
-    int G = 1;
-    while (G < 32 && G * 2 * nout <= SC_THREADS) G *= 2;
-    const int part = tid % G, og = tid / G, ngroups = SC_THREADS / G;
-
-    for (int t = 0; t < NK; ++t) {
-        issue(t + STAGES - 1);
-        cp_wait<STAGES - 1>();
-        __syncthreads();
-        const cx<T>* Uk = ust + (size_t)(t % STAGES) * Rmax * max_m;  // rows r0.. of U_i, [nr][m]
-        cx<T>* out = xb + (size_t)(t & 1) * xbs;
-        if (fwd) {
-            // rows of psi: out[r][o - r0] = sum_j U[o][j] x[r][j]
+    // forward: out[r][ra + ol] = sum_j U[r0 + ra + ol][j] x[r][j];
+    // backward: out[r][o] (first pass) = or += sum_{ii < rn} conj(U[r0 + ra + ii][o]) x[r][r0 + ra + ii]
+    auto compute = [&](const cx<T>* Uk, int ra, int rn, int lg, bool first, cx<T>* out) {
+        const int G = 1 << lg, part = tid & (G - 1), og = tid >> lg, ngroups = SC_THREADS >> lg;
+        const int nout = fwd ? rn * c : m * c;
+        if (SUB && fwd && lg > 5) {
+            // one pass: warp sums, then the group's warps through shared memory
+            const int e = og;
+            const int r = e < nout ? e / rn : 0, ol = e < nout ? e - r * rn : 0;
+            cx<T> acc = mk<T>(0, 0);
+            if (e < nout) {
+                const cx<T>* row = Uk + (size_t)ol * m;
+                const cx<T>* xr = x + (size_t)r * max_m;
+                for (int j = part; j < m; j += G) cfma<T>(acc, row[j], xr[j]);
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
+            }
+            if ((tid & 31) == 0) red[tid >> 5] = acc;
+            __syncthreads();
+            if (e < nout && part == 0) {
+                for (int w = 1; w < G / 32; ++w) {
+                    acc.x += red[(tid >> 5) + w].x;
+                    acc.y += red[(tid >> 5) + w].y;
+                }
+                out[(size_t)r * max_m + ra + ol] = acc;
+            }
+        } else if (fwd) {
             for (int o0 = 0; o0 < nout; o0 += ngroups) {
                 const int e = o0 + og;
                 cx<T> acc = mk<T>(0, 0);
                 int r = 0, ol = 0;
                 if (e < nout) {
-                    r = e / nr;
-                    ol = e - r * nr;
+                    r = e / rn;
+                    ol = e - r * rn;
                     const cx<T>* row = Uk + (size_t)ol * m;
                     const cx<T>* xr = x + (size_t)r * max_m;
                     for (int j = part; j < m; j += G) cfma<T>(acc, row[j], xr[j]);
@@ -137,10 +153,9 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
                 }
-                if (e < nout && part == 0) out[(size_t)r * max_m + ol] = acc;
+                if (e < nout && part == 0) out[(size_t)r * max_m + ra + ol] = acc;
             }
         } else {
-            // partial sums over this CTA's rows: out[r][o] = sum_{ii in rows} conj(U[ii][o]) x[r][ii]
             for (int o0 = 0; o0 < nout; o0 += ngroups) {
                 const int e = o0 + og;
                 cx<T> acc = mk<T>(0, 0);
@@ -148,16 +163,27 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
                 if (e < nout) {
                     r = e / m;
                     o = e - r * m;
-                    const cx<T>* xr = x + (size_t)r * max_m;
-                    for (int ii = part; ii < nr; ii += G) cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[r0 + ii]);
+                    const cx<T>* xr = x + (size_t)r * max_m + r0 + ra;
+                    for (int ii = part; ii < rn; ii += G) cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[ii]);
                 }
                 for (int off = G / 2; off > 0; off >>= 1) {
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, off);
                 }
-                if (e < nout && part == 0) out[(size_t)r * max_m + o] = acc;
+                if (e < nout && part == 0) {
+                    cx<T>& d = out[(size_t)r * max_m + o];
+                    if (!SUB || first) d = acc;
+                    else {
+                        d.x += acc.x;
+                        d.y += acc.y;
+                    }
+                }
             }
         }
+    };
+    // after step t: the cluster barrier, then the next input vector (and its stored slot) from the
+    // exchange buffers out of every CTA of the cluster
+    auto exchange = [&](int t, cx<T>* out) {
         cluster_sync_all();  // exchange buffers of step t complete in every CTA of the cluster
         const int i = fwd ? t : NK - 1 - t;
         const long long ks = fwd ? i + 1 : i;
@@ -186,6 +212,72 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
             }
         }
         __syncthreads();
+    };
+
+    if constexpr (!SUB) {
+        // all of a step's rows in one ring slot, issued STAGES - 1 steps ahead of use
+        auto issue = [&](int t) {
+            if (t < NK && nr > 0) {
+                const int i = fwd ? t : NK - 1 - t;
+                const cx<T>* src = U + B.u_off + (long long)i * mmp + (long long)r0 * m;
+                cx<T>* dst = ust + (size_t)(t % STAGES) * RS * max_m;
+                for (int e = tid; e < nr * m; e += SC_THREADS) cp_async(dst + e, src + e);
+            }
+            cp_commit();
+        };
+        for (int t = 0; t < STAGES - 1; ++t) issue(t);
+        __syncthreads();
+        const int lg = split(fwd ? nr * c : m * c);
+        for (int t = 0; t < NK; ++t) {
+            issue(t + STAGES - 1);
+            cp_wait<STAGES - 1>();
+            __syncthreads();
+            cx<T>* out = xb + (size_t)(t & 1) * xbs;
+            compute(ust + (size_t)(t % STAGES) * RS * max_m, 0, nr, lg, true, out);
+            exchange(t, out);
+        }
+    } else {
+        // sub-blocks of RS rows, issued STAGES - 1 sub-blocks ahead of use
+        const int nsb = nr > 0 ? (nr + RS - 1) / RS : 0;
+        int it = 0, isb = 0, islot = 0;  // next sub-block to issue: step, index, ring slot
+        auto issue = [&]() {
+            if (nsb > 0 && it < NK) {
+                const int i = fwd ? it : NK - 1 - it;
+                const int ra = isb * RS, rn = min(RS, nr - ra);
+                const cx<T>* src = U + B.u_off + (long long)i * mmp + (long long)(r0 + ra) * m;
+                cx<T>* dst = ust + (size_t)islot * RS * max_m;
+                for (int e = tid; e < rn * m; e += SC_THREADS) cp_async(dst + e, src + e);
+                if (++isb == nsb) {
+                    isb = 0;
+                    ++it;
+                }
+                if (++islot == STAGES) islot = 0;
+            }
+            cp_commit();
+        };
+        for (int g = 0; g < STAGES - 1; ++g) issue();
+        __syncthreads();
+        const int rn_last = nr - (nsb - 1) * RS;
+        const int lg_full = split(fwd ? RS * c : m * c), lg_last = split(fwd ? rn_last * c : m * c);
+        int cslot = 0;  // ring slot of the sub-block in use
+        for (int t = 0; t < NK; ++t) {
+            cx<T>* out = xb + (size_t)(t & 1) * xbs;
+            if (!fwd && nsb == 0)  // no rows: this CTA's partial sums are zero
+                for (int e = tid; e < m * c; e += SC_THREADS) out[(size_t)(e / m) * max_m + e % m] = mk<T>(0, 0);
+            for (int sb = 0; sb < nsb; ++sb) {
+                issue();
+                cp_wait<STAGES - 1>();
+                __syncthreads();
+                const bool last = sb + 1 == nsb;
+                compute(ust + (size_t)cslot * RS * max_m, sb * RS, last ? rn_last : RS, last ? lg_last : lg_full,
+                        sb == 0, out);
+                if (++cslot == STAGES) cslot = 0;
+                // the slot is refilled and out is extended by the next sub-block (after the last one of
+                // the step the cluster barrier orders both)
+                if (!last) __syncthreads();
+            }
+            exchange(t, out);
+        }
     }
     cp_wait<0>();
     // final vector (own range) to the boundary output
@@ -198,82 +290,124 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
 }
 
 template <class T, int STAGES>
-size_t sc_smem(int max_m, int max_c, int CL) {
+size_t sc_smem(int max_m, int max_c, int RS) {
+    return ((size_t)STAGES * RS * max_m + 3 * (size_t)max_c * max_m) * sizeof(cx<T>);
+}
+
+constexpr size_t SC_SMEM_LIMIT = 220 * 1024;
+
+// rows per ring slot: all of a CTA's rows when the ring holds them, else as many as fit (0: none)
+template <class T, int STAGES>
+int sc_rows_per_slot(int max_m, int max_c, int CL) {
     const int Rmax = (max_m + CL - 1) / CL;
-    return ((size_t)STAGES * Rmax * max_m + 3 * (size_t)max_c * max_m) * sizeof(cx<T>);
+    const size_t fixed = 3 * (size_t)max_c * max_m * sizeof(cx<T>);
+    if (fixed >= SC_SMEM_LIMIT) return 0;
+    const size_t per_row = (size_t)STAGES * max_m * sizeof(cx<T>);
+    const long long rs = (long long)((SC_SMEM_LIMIT - fixed) / per_row);
+    return (int)std::min<long long>(Rmax, rs);
+}
+
+// Ring shape for a cluster of CL: 8 slots of all a CTA's rows when they fit (whole-row mode), else
+// (large blocks) 4 slots of as many rows as fit (sub-block mode).  Returns the slots (0: the kernel
+// does not fit) and the rows per slot.
+template <class T>
+int sc_shape(int max_m, int max_c, int CL, int* RS) {
+    const int Rmax = (max_m + CL - 1) / CL;
+    *RS = sc_rows_per_slot<T, 8>(max_m, max_c, CL);
+    if (*RS == Rmax) return 8;
+    *RS = sc_rows_per_slot<T, 4>(max_m, max_c, CL);
+    return *RS >= 1 ? 4 : 0;
 }
 
 template <class T, int STAGES>
-int sc_launch(const DevPlan& P, const void* U, const void* fi, void* fo, const void* bi, void* bo, void* ps, void* ls,
-              int dirs, int CL, int max_m, int max_c, int nchains, cudaStream_t st) {
-    const size_t sm = sc_smem<T, STAGES>(max_m, max_c, CL);
-    auto kern = sweep_cluster_kernel<T, STAGES>;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+cudaLaunchConfig_t sc_config(int CL, int nchains, size_t sm, cudaStream_t st, cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3((unsigned)(nchains * CL));
     cfg.blockDim = dim3(SC_THREADS);
     cfg.dynamicSmemBytes = sm;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = (unsigned)CL;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <class T, int STAGES, bool SUB>
+int sc_launch(const DevPlan& P, const void* U, const void* fi, void* fo, const void* bi, void* bo, void* ps, void* ls,
+              int dirs, int CL, int max_m, int max_c, int RS, int nchains, cudaStream_t st) {
+    const size_t sm = sc_smem<T, STAGES>(max_m, max_c, RS);
+    auto kern = sweep_cluster_kernel<T, STAGES, SUB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) return -1;
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = sc_config<T, STAGES>(CL, nchains, sm, st, attr);
     const cudaError_t e = cudaLaunchKernelEx(&cfg, kern, P, (const cx<T>*)U, (const cx<T>*)fi, (cx<T>*)fo,
                                              (const cx<T>*)bi, (cx<T>*)bo, (cx<T>*)ps, (cx<T>*)ls, dirs, CL, max_m,
-                                             max_c);
+                                             max_c, RS);
     return e == cudaSuccess ? 0 : -1;
 }
 
-constexpr size_t SC_SMEM_LIMIT = 220 * 1024;
+// clusters of CL CTAs that the GPU holds at once (0 on error)
+template <class T, int STAGES, bool SUB>
+int sc_resident(int CL, int nchains, int max_m, int max_c, int RS) {
+    const size_t sm = sc_smem<T, STAGES>(max_m, max_c, RS);
+    auto kern = sweep_cluster_kernel<T, STAGES, SUB>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchAttribute attr[1];
+    const cudaLaunchConfig_t cfg = sc_config<T, STAGES>(CL, nchains, sm, 0, attr);
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return n;
+}
+
+template <class T>
+int sc_resident_any(int CL, int nchains, int max_m, int max_c) {
+    int RS = 0;
+    const int S = sc_shape<T>(max_m, max_c, CL, &RS);
+    if (S == 8) return sc_resident<T, 8, false>(CL, nchains, max_m, max_c, RS);
+    if (S == 4) return sc_resident<T, 4, true>(CL, nchains, max_m, max_c, RS);
+    return 0;
+}
+
+template <class T>
+int sc_launch_any(const DevPlan& P, const void* U, const void* fi, void* fo, const void* bi, void* bo, void* ps,
+                  void* ls, int dirs, int CL, int max_m, int max_c, int nchains, cudaStream_t st) {
+    int RS = 0;
+    const int S = sc_shape<T>(max_m, max_c, CL, &RS);
+    if (S == 8) return sc_launch<T, 8, false>(P, U, fi, fo, bi, bo, ps, ls, dirs, CL, max_m, max_c, RS, nchains, st);
+    if (S == 4) return sc_launch<T, 4, true>(P, U, fi, fo, bi, bo, ps, ls, dirs, CL, max_m, max_c, RS, nchains, st);
+    return -1;
+}
 
 }  // namespace
 
 int sweep_cluster_fits(int prec, int max_m, int max_c, int CL) {
-    const size_t sm = prec == QOC_PREC_F64 ? sc_smem<double, 8>(max_m, max_c, CL) : sc_smem<float, 8>(max_m, max_c, CL);
-    return sm <= SC_SMEM_LIMIT;
+    int RS = 0;
+    return (prec == QOC_PREC_F64 ? sc_shape<double>(max_m, max_c, CL, &RS) : sc_shape<float>(max_m, max_c, CL, &RS)) > 0;
 }
 
 // Cluster size for the sweeps of a plan with nb active blocks (0: use the one-CTA-per-chain kernel).
 // Every chain must find its cluster resident at once: chains x CL CTAs within the GPU's clusters.
+// Sizes 8 down to 2 are tried (any size, so that e.g. 20 chains can take clusters of 7).
 int sweep_cluster_size(int prec, int nb, int max_m, int max_c) {
     if (max_m < 24 || nb < 1) return 0;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int chains = 2 * nb;
-    for (int CL = 8; CL >= 2; CL /= 2) {
+    for (int CL = 8; CL >= 2; --CL) {
         if (chains * CL > sms) continue;
-        const size_t sm = prec == QOC_PREC_F64 ? sc_smem<double, 8>(max_m, max_c, CL) : sc_smem<float, 8>(max_m, max_c, CL);
-        if (sm > SC_SMEM_LIMIT) continue;
-        // clusters of this shape that the GPU holds at once
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3((unsigned)(chains * CL));
-        cfg.blockDim = dim3(SC_THREADS);
-        cfg.dynamicSmemBytes = sm;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = (unsigned)CL;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int nclu = 0;
-        cudaError_t e;
-        if (prec == QOC_PREC_F64) {
-            cudaFuncSetAttribute(sweep_cluster_kernel<double, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            e = cudaOccupancyMaxActiveClusters(&nclu, sweep_cluster_kernel<double, 8>, &cfg);
-        } else {
-            cudaFuncSetAttribute(sweep_cluster_kernel<float, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            e = cudaOccupancyMaxActiveClusters(&nclu, sweep_cluster_kernel<float, 8>, &cfg);
-        }
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (nclu >= chains) return CL;
+        const int n = prec == QOC_PREC_F64 ? sc_resident_any<double>(CL, chains, max_m, max_c)
+                                           : sc_resident_any<float>(CL, chains, max_m, max_c);
+        if (n >= chains) return CL;
     }
     return 0;
 }
@@ -284,10 +418,10 @@ int launch_sweeps_cluster(const DevPlan& P, const void* U, const void* fwd_init,
     const int nchains = ((dirs & 1) ? P.nb : 0) + ((dirs & 2) ? P.nb : 0);
     if (nchains == 0) return 0;
     if (P.prec == QOC_PREC_F64)
-        return sc_launch<double, 8>(P, U, fwd_init, fwd_out, bwd_init, bwd_out, psi_store, lam_store, dirs, CL, max_m,
-                                    max_c, nchains, st);
-    return sc_launch<float, 8>(P, U, fwd_init, fwd_out, bwd_init, bwd_out, psi_store, lam_store, dirs, CL, max_m, max_c,
-                               nchains, st);
+        return sc_launch_any<double>(P, U, fwd_init, fwd_out, bwd_init, bwd_out, psi_store, lam_store, dirs, CL, max_m,
+                                     max_c, nchains, st);
+    return sc_launch_any<float>(P, U, fwd_init, fwd_out, bwd_init, bwd_out, psi_store, lam_store, dirs, CL, max_m,
+                                max_c, nchains, st);
 }
 
 }  // namespace qoc

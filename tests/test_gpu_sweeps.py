@@ -78,7 +78,46 @@ def test_cluster_sweeps_in_checkpoint_windows():
 def test_cluster_size_rejections():
     s = I.xxz_ring(8, 3.0, 10)
     _, _, _, plan, _, _ = _setup(s, 409, "f32")
-    with pytest.raises(Exception):
-        plan.set_sweep_cluster(3)
+    for bad in (1, 9, -2):
+        with pytest.raises(Exception):
+            plan.set_sweep_cluster(bad)
+    plan.set_sweep_cluster(3)
+    assert plan.sweep_cluster() == 3
     plan.set_sweep_cluster(-1)
-    assert plan.sweep_cluster() in (0, 2, 4, 8)
+    assert plan.sweep_cluster() in (0, 2, 3, 4, 5, 6, 7, 8)
+
+
+@pytest.mark.parametrize("prec,cl", [("f64", 3), ("f64", 8), ("f32", 5), ("f32", 8)])
+def test_cluster_sweeps_stream_large_blocks_in_row_subblocks(prec, cl):
+    # D_12 blocks of up to 346 states: a CTA's rows of U_k exceed the 8-slot ring, so they pass
+    # through 4 slots in sub-blocks (ragged last one); states against the oracle's per-block
+    # propagation, F and dF/du against the one-CTA-per-chain kernel
+    s = I.xxz_ring(12, 2.0, 8)
+    dim = 2 ** s.n
+    B = api.Basis(s)
+    b0 = B.state_to_blocks(I.random_state(411, dim))
+    bf = B.state_to_blocks(I.random_state(412, dim))
+    plan = api.Plan(B, s.N, s.tau, prec=prec)
+    d0, df = api.to_device(b0, DEV), api.to_device(bf, DEV)
+    un = I.pulses_normal(31, s.N, 3)
+    u = torch.from_numpy(un).to(DEV)
+    plan.set_sweep_cluster(0)
+    o_1, g_1 = _fg(plan, u, d0, df)
+    plan.set_sweep_cluster(cl)
+    o_c, g_c = _fg(plan, u, d0, df)
+    psiN = plan.propagate(u, d0)
+    torch.cuda.synchronize()
+    psiN = psiN.cpu().numpy()
+    ov, err = 0.0 + 0.0j, 0.0
+    for b, (_, m, c, off) in enumerate(B.blocks):
+        h0, hc = B.block_matrices(b)
+        x0 = b0[off:off + c * m].reshape(c, m).T
+        ref = gr.forward_states(gr.propagators(dict(h0=h0, hc=list(hc)), un, s.tau), x0)[-1]
+        got = psiN[off:off + c * m].reshape(c, m).T
+        err = max(err, np.abs(got - ref).max())
+        ov += np.vdot(bf[off:off + c * m].reshape(c, m).T, ref)
+    tol = TOL[prec]
+    assert err <= (1e-11 if prec == "f64" else 2e-5)
+    assert abs(o_c[0] - abs(ov) ** 2) <= tol
+    assert abs(o_c[0] - o_1[0]) <= (1e-13 if prec == "f64" else 1e-6)
+    assert np.linalg.norm(g_c - g_1) / np.linalg.norm(g_1) <= (1e-12 if prec == "f64" else 1e-5)
