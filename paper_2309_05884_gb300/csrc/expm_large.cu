@@ -3,20 +3,26 @@
 //
 // The Taylor polynomial of odd degree 2q-1 is evaluated by Horner's rule in Y = X^2 (as in
 // expm_tc.cu), T(X) = sum_{j<q} (c_{2j} I + c_{2j+1} X) Y^j, but a block no longer fits one CTA: every
-// product is a batched tiled GEMM launch over (128 x 128 output tile, slice), with the matrices of
-// a chunk of slices in a global scratch area (X, Y and two Horner iterates per slice, FP32).
+// product is a batched tiled GEMM launch over (128 x 128 output tile, slice), with the operands of a
+// chunk of slices in a global scratch area.
 //   xl_prep      per slice: norm bound, Taylor degree, power-of-two operand scales, ownership (slices
 //                that need squarings are left to the CUDA-core tiles);
-//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j);
-//   xl_gemm      Y = X X, then S <- S Y + c_{2j+1} X + c_{2j} I for j = q-2 .. 0 (a slice joins at its
-//                own first step, where S = c_{2q-1} X + c_{2q-2} I is formed while staging);
-//   xl_export    U = T(X) into the propagator store.
-// GEMM tile: one CTA of 512 threads, M = N = 128, K in chunks of 32 through two shared-memory stages.
-// Each stage holds the FP16 hi/lo split of a 128 x 32 slab of A (rows, K-major) and of B^T (rows of
-// B^T, staged transposed from B's rows), with the power-of-two operand scales of the slice; the MMAs
-// of a chunk run while the next chunk is staged.  The (hi,hi) products accumulate in one pair of TMEM
-// accumulators and the three smaller split products in another, added in FP32 at the end: with K up
-// to 2048 the small terms are never rounded against the large running sum.
+//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j) in FP32, and the split operand planes of X (both
+//                sides) and of S = c_{2q-1} X + c_{2q-2} I;
+//   xl_gemm      Y^T = X^T X^T, then S <- S Y + c_{2j+1} X + c_{2j} I for j = q-2 .. 0; the last step
+//                writes U = T(X) into the propagator store;
+//   xl_export    U = I + X for the slices of degree 1.
+// Operands live in global memory already split: an m x m matrix padded to mp = 128 ceil(m / 128) is
+// a grid of slabs (128-row tile t, 32-wide K chunk), each four FP16 planes (re hi, re lo, im hi, im
+// lo) of 128 x 32 in the K-major no-swizzle core layout that the MMA descriptors read, 32 KB in one
+// piece.  "A side" slabs hold rows of the matrix, "B side" slabs rows of its transpose.  The GEMM
+// main loop is then only bulk copies (one per operand and chunk) into a 3-stage shared-memory ring
+// and MMAs: one thread keeps the copies two chunks ahead of the MMAs and refills a stage as soon as
+// the MMAs that read it commit.  Epilogues write the planes the next product reads; Y is formed
+// transposed, so that its B-side slabs are written as rows like every other output.  The (hi, hi)
+// products accumulate in one pair of TMEM accumulators and the three smaller split products in
+// another, added in FP32 at the end: with K up to 2048 the small terms are never rounded against the
+// large running sum.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -29,9 +35,12 @@ namespace qoc {
 namespace {
 
 constexpr int XL_THREADS = 512;
-constexpr int XL_TM = 128, XL_TN = 128, XL_KC = 32;
+constexpr int XL_TM = 128, XL_KC = 32, XL_STAGES = 3;
 constexpr uint64_t XL_WAIT_NS = 2000000000ull;
 constexpr uint32_t XL_TMEM_COLS = 512;  // re, im of the (hi,hi) and of the correction accumulators
+constexpr uint32_t XL_PLANE = XL_TM * XL_KC * 2;  // bytes of one FP16 plane of a slab (8 KB)
+constexpr uint32_t XL_SLAB = 4 * XL_PLANE;        // one slab: four planes (32 KB)
+constexpr uint32_t XL_STAGE = 2 * XL_SLAB;        // one ring stage: an A slab and a B slab
 
 // 1/k!, k = 0..35 (Taylor coefficients)
 __constant__ float xl_coef[36] = {
@@ -60,6 +69,50 @@ __device__ __forceinline__ int xl_off(int row, int k) { return (((row >> 3) * (X
 __device__ __forceinline__ void xl_split(float x, __half& hi, __half& lo) {
     hi = __float2half_rn(x);
     lo = __float2half_rn(x - __half2float(hi));
+}
+
+// padded size of a block: whole 128-row tiles
+__host__ __device__ __forceinline__ int xl_pad(int m) { return (m + XL_TM - 1) / XL_TM * XL_TM; }
+
+// byte offset of slab (tile t, K chunk ch) in a plane set of padded size mp
+__device__ __forceinline__ size_t xl_slab(int t, int ch, int mp) {
+    return ((size_t)t * (mp / XL_KC) + ch) * XL_SLAB;
+}
+
+// Eight consecutive K entries v[0..8) of one slab row, scaled by s, split into the four planes at
+// halves offset off (a multiple of 8: 16 bytes per plane).  Returns false if a scaled entry leaves
+// the FP16 range.
+__device__ __forceinline__ bool xl_put8(unsigned char* slab, int off, const float2 (&v)[8], float s) {
+    __half h[4][8];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float re = v[c].x * s, im = v[c].y * s;
+        ok = ok && fabsf(re) < 65504.f && fabsf(im) < 65504.f;
+        xl_split(re, h[0][c], h[1][c]);
+        xl_split(im, h[2][c], h[3][c]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint4*>(slab + p * XL_PLANE + off * 2) = *reinterpret_cast<const uint4*>(h[p]);
+    return ok;
+}
+
+// Scratch of one slice: X in FP32 [m][m] (xbytes), then five plane sets of pbytes each.
+struct XlMats {
+    float2* X;
+    unsigned char *XA, *XB, *YT, *S0, *S1;  // X (A side), X (B side), Y (B side) = Y^T (A side), S ping-pong
+};
+__device__ __forceinline__ XlMats xl_mats(unsigned char* scratch, int slice, size_t xbytes, size_t pbytes) {
+    unsigned char* b = scratch + (size_t)slice * (xbytes + 5 * pbytes);
+    XlMats M;
+    M.X = reinterpret_cast<float2*>(b);
+    M.XA = b + xbytes;
+    M.XB = M.XA + pbytes;
+    M.YT = M.XB + pbytes;
+    M.S0 = M.YT + pbytes;
+    M.S1 = M.S0 + pbytes;
+    return M;
 }
 
 // Prep: one thread per slice of the chunk [i0, i0 + n) of the class's item range.
@@ -111,13 +164,18 @@ __global__ void xl_prep_kernel(DevPlan P, ExpmTables tabs, const double* __restr
     items[t] = X;
 }
 
-// X = -i sc (H0 + sum_j u_j Hc_j) for every owned slice: grid (chunks of entries, slice).
+// For every owned slice (grid: chunks of groups, slice): X = -i sc (H0 + sum_j u_j Hc_j) in FP32 and
+// the planes of X on both sides (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I on the A
+// side (scale 2^eS, in S1 where the first Horner step reads it), zero outside the m x m block.  A
+// group is eight consecutive K entries of one slab row: first the A-side groups (row r, entries
+// (r, 8g..8g+7)), then the B-side ones (row n of X^T, entries X[8g..8g+7][n]; n runs fastest so
+// that the column reads of H coalesce).
 __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __restrict__ items,
-                                   float2* __restrict__ scratch, size_t slot) {
+                                   unsigned char* __restrict__ scratch, size_t xbytes, size_t pbytes) {
     const XlItem& X = items[blockIdx.y];
     if (!X.own) return;
     const DevBlock& B = P.blocks[X.bi];
-    const int m = B.m;
+    const int m = B.m, mp = xl_pad(m), ng = mp / 8;
     const size_t mm = (size_t)m * m;
     const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
     float uf[8];
@@ -125,95 +183,62 @@ __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, cons
         const double x = u[(size_t)(B.u_row + X.k) * P.nc + j];
         uf[j] = isfinite(x) ? (float)x : 0.f;
     }
-    float2* Xm = scratch + (size_t)blockIdx.y * 4 * slot;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
+    const XlMats M = xl_mats(scratch, blockIdx.y, xbytes, pbytes);
+    const float sX = ldexpf(1.f, X.eX), sS = ldexpf(1.f, X.eS);
+    const float c1 = xl_coef[2 * X.q - 1], c0 = xl_coef[2 * X.q - 2];
+    auto xval = [&](int r, int k) {  // X[r][k], 0 outside the block
+        if (r >= m || k >= m) return make_float2(0.f, 0.f);
+        const size_t e = (size_t)r * m + k;
         float2 h = H[e];
         for (int j = 0; j < P.nc; ++j) {
             const float2 hc = H[(size_t)(1 + j) * mm + e];
             h.x = fmaf(uf[j], hc.x, h.x);
             h.y = fmaf(uf[j], hc.y, h.y);
         }
-        Xm[e] = make_float2(h.y * X.sc, -h.x * X.sc);
-    }
-}
-
-// One K chunk [k0, k0 + XL_KC) of the A rows [row0, row0 + 128) and of the B^T rows (B columns)
-// [col0, col0 + 128), held in registers between its load and its store into a stage: each thread
-// loads 8 consecutive k of one A row (thread t: row t / 4) and 8 consecutive rows of B at one column
-// (t % 128; coalesced along the columns).  Entries outside the m x m matrix are 0; A is
-// S_init = c1 X + c0 I when init (X in Asrc).
-struct XlRegs {
-    float2 a[8], b[8];
-};
-
-__device__ __forceinline__ void xl_load(XlRegs& R, const float2* __restrict__ Asrc, const float2* __restrict__ Bsrc,
-                                        int m, int row0, int col0, int k0, bool init, float c1, float c0) {
-    const int t = threadIdx.x;
-    {
-        const int r = row0 + (t >> 2), kb = k0 + (t & 3) * 8;
+        return make_float2(h.y * X.sc, -h.x * X.sc);
+    };
+    const long long G = (long long)mp * ng;
+    bool ok = true;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * G;
+         idx += (long long)gridDim.x * blockDim.x) {
+        float2 v[8];
+        if (idx < G) {
+            const int r = (int)(idx / ng), g = (int)(idx - (long long)r * ng);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int k = kb + c;
-            float2 v = make_float2(0.f, 0.f);
-            if (r < m && k < m) {
-                v = Asrc[(size_t)r * m + k];
-                if (init) {
-                    v.x = c1 * v.x + (r == k ? c0 : 0.f);
-                    v.y = c1 * v.y;
+            for (int c = 0; c < 8; ++c) v[c] = xval(r, 8 * g + c);
+            if (r < m)
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (8 * g + c < m) M.X[(size_t)r * m + 8 * g + c] = v[c];
+            const size_t sl = xl_slab(r / XL_TM, (8 * g) / XL_KC, mp);
+            const int off = xl_off(r % XL_TM, (8 * g) % XL_KC);
+            ok = xl_put8(M.XA + sl, off, v, sX) && ok;
+            if (X.q >= 2) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    v[c].x = c1 * v[c].x + (r == 8 * g + c && r < m ? c0 : 0.f);
+                    v[c].y = c1 * v[c].y;
                 }
+                ok = xl_put8(M.S1 + sl, off, v, sS) && ok;
             }
-            R.a[c] = v;
+        } else {
+            const long long i2 = idx - G;
+            const int g = (int)(i2 / mp), n = (int)(i2 - (long long)g * mp);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) v[c] = xval(8 * g + c, n);
+            ok = xl_put8(M.XB + xl_slab(n / XL_TM, (8 * g) / XL_KC, mp), xl_off(n % XL_TM, (8 * g) % XL_KC), v, sX) && ok;
         }
     }
-    {
-        const int n = col0 + (t & 127), kb = k0 + (t >> 7) * 8;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            const int k = kb + c;
-            R.b[c] = (n < m && k < m) ? Bsrc[(size_t)k * m + n] : make_float2(0.f, 0.f);
-        }
-    }
-}
-
-// The registers of one chunk into the FP16 planes of a stage (A: planes 0..3 = re hi, re lo, im hi,
-// im lo; B^T: planes 4..7), scaled by the power-of-two scales sA and sB.
-__device__ __forceinline__ void xl_store(unsigned char* st, const XlRegs& R, float sA, float sB) {
-    __half* pl = reinterpret_cast<__half*>(st);
-    constexpr int PL = XL_TM * XL_KC;  // halves per plane
-    const int t = threadIdx.x;
-    {
-        __half h[4][8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            xl_split(R.a[c].x * sA, h[0][c], h[1][c]);
-            xl_split(R.a[c].y * sA, h[2][c], h[3][c]);
-        }
-        const int off = xl_off(t >> 2, (t & 3) * 8);
-#pragma unroll
-        for (int p = 0; p < 4; ++p) *reinterpret_cast<uint4*>(pl + p * PL + off) = *reinterpret_cast<const uint4*>(h[p]);
-    }
-    {
-        __half h[4][8];
-#pragma unroll
-        for (int c = 0; c < 8; ++c) {
-            xl_split(R.b[c].x * sB, h[0][c], h[1][c]);
-            xl_split(R.b[c].y * sB, h[2][c], h[3][c]);
-        }
-        const int off = xl_off(t & 127, (t >> 7) * 8);
-#pragma unroll
-        for (int p = 0; p < 4; ++p)
-            *reinterpret_cast<uint4*>(pl + (4 + p) * PL + off) = *reinterpret_cast<const uint4*>(h[p]);
-    }
+    if (!ok) atomicOr(P.status, ST_RANGE);
 }
 
 // One thread: the MMAs of one staged chunk.  Corrections (lo lo, hi lo, lo hi) into (cre, cim), the
 // (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
 __device__ __forceinline__ void xl_issue(uint32_t st, bool first, uint32_t hre, uint32_t him, uint32_t cre, uint32_t cim) {
-    constexpr uint32_t PLB = XL_TM * XL_KC * 2;  // plane bytes
     const uint32_t lbo = 128, sbo = (XL_KC / 8) * 128;
-    const uint32_t pos = idesc_f16(XL_TM, XL_TN, false), neg = idesc_f16(XL_TM, XL_TN, true);
-    const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + 4 * PLB, lbo, sbo);
-    const uint64_t pl = PLB >> 4;
+    const uint32_t pos = idesc_f16(XL_TM, XL_TM, false), neg = idesc_f16(XL_TM, XL_TM, true);
+    const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + XL_SLAB, lbo, sbo);
+    const uint64_t pl = XL_PLANE >> 4;
     const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};  // (lo,lo), (hi,lo), (lo,hi), (hi,hi)
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
@@ -232,51 +257,46 @@ __device__ __forceinline__ void xl_issue(uint32_t st, bool first, uint32_t hre, 
     }
 }
 
-// C = A B for every owned slice of the chunk: grid (output tiles of the largest block, slice).
-// mode 0: Y = X X.  mode 1: Horner step j: S_out = S_in Y + c_{2j+1} X + c_{2j} I for slices with
-// j <= q - 2 (at j = q - 2, S_in = c_{2q-1} X + c_{2q-2} I is formed while staging).
+// One product for every owned slice of degree q >= 2 in the chunk: grid (128 x 128 output tiles of
+// the largest block, slice).  mode 0: Y^T = X^T X^T (A = X B side, B = X A side), written as the A
+// side of Y^T, i.e. the B side of Y, at scale 2^eY.  mode 1: Horner step j (slices with j <= q - 2):
+// S_out = S_in Y + c_{2j+1} X + c_{2j} I from S[(q-1-j) & 1] into S[(q-2-j) & 1] at scale 2^eS, or
+// for j = 0 into the propagator store U_b[kw] (FP32, m x m).
 __global__ void __launch_bounds__(XL_THREADS, 1)
-xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, float2* __restrict__ scratch, size_t slot, int tiles_n,
-               int mode, int j) {
+xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch, size_t xbytes,
+               size_t pbytes, int tiles_n, int mode, int j, float2* __restrict__ Uout) {
     extern __shared__ __align__(1024) unsigned char sm[];
-    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ __align__(8) uint64_t full[XL_STAGES], empty[XL_STAGES], done;
     __shared__ uint32_t tslot;
+    __shared__ int s_fail;
     const XlItem& X = items[blockIdx.y];
-    if (!X.own) return;
+    if (!X.own || X.q < 2) return;
     if (mode == 1 && j > X.q - 2) return;
     const DevBlock& B = P.blocks[X.bi];
-    const int m = B.m;
+    const int m = B.m, mp = xl_pad(m);
     const int tm = blockIdx.x / tiles_n, tn = blockIdx.x % tiles_n;
-    const int row0 = tm * XL_TM, col0 = tn * XL_TN;
-    if (row0 >= m || col0 >= m) return;
+    const int row0 = tm * XL_TM, col0 = tn * XL_TM;
+    if (row0 >= mp || col0 >= mp) return;
 
-    float2* base = scratch + (size_t)blockIdx.y * 4 * slot;
-    float2* Xm = base;
-    float2* Ym = base + slot;
-    const float2* Asrc;
-    const float2* Bsrc;
-    float2* Cdst;
-    float sA, sB, unscale, c1 = 0.f, c0 = 0.f, ic1 = 0.f, ic0 = 0.f;
-    bool init = false;
+    const XlMats M = xl_mats(scratch, blockIdx.y, xbytes, pbytes);
+    const unsigned char *Apl, *Bpl;
+    unsigned char* Opl = nullptr;
+    float unscale, sout = 1.f, c1 = 0.f, c0 = 0.f;
     if (mode == 0) {
-        Asrc = Xm;
-        Bsrc = Xm;
-        Cdst = Ym;
-        sA = sB = ldexpf(1.f, X.eX);
+        Apl = M.XB;
+        Bpl = M.XA;
+        Opl = M.YT;
         unscale = ldexpf(1.f, -2 * X.eX);
+        sout = ldexpf(1.f, X.eY);
     } else {
         const int out = (X.q - 2 - j) & 1;
-        init = j == X.q - 2;
-        Asrc = init ? Xm : base + (size_t)(2 + (out ^ 1)) * slot;
-        Bsrc = Ym;
-        Cdst = base + (size_t)(2 + out) * slot;
-        sA = ldexpf(1.f, X.eS);
-        sB = ldexpf(1.f, X.eY);
+        Apl = out ? M.S0 : M.S1;
+        Bpl = M.YT;
+        if (j > 0) Opl = out ? M.S1 : M.S0;
         unscale = ldexpf(1.f, -(X.eS + X.eY));
+        sout = ldexpf(1.f, X.eS);
         c1 = xl_coef[2 * j + 1];
         c0 = xl_coef[2 * j];
-        ic1 = xl_coef[2 * X.q - 1];
-        ic0 = xl_coef[2 * X.q - 2];
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -285,8 +305,11 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, float2* __restrict__
         tmem_relinquish();
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < XL_STAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&done, 1);
         fence_mbar_init();
     }
     tc_fence_before();
@@ -294,103 +317,127 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, float2* __restrict__
     tc_fence_after();
     const uint32_t tmem = tslot;
     const uint32_t hre = tmem, him = tmem + 128, cre = tmem + 256, cim = tmem + 384;
-    constexpr uint32_t STAGE = 8 * XL_TM * XL_KC * 2;  // 8 planes of FP16
     const uint32_t sbase = smem_u32(sm);
-    const int nch = (m + XL_KC - 1) / XL_KC;
-    bool failed = false;
-    // chunk ch + 1 is loaded into registers while the MMAs of chunks ch - 1 and ch run
-    XlRegs R;
-    xl_load(R, Asrc, Bsrc, m, row0, col0, 0, init, ic1, ic0);
-    for (int ch = 0; ch < nch && !failed; ++ch) {
-        const int stg = ch & 1;
-        if (ch >= 2) {  // the MMAs of chunk ch - 2 read this stage
-            const bool ok = mbar_wait_bounded(&bar[stg], (uint32_t)(((ch - 2) >> 1) & 1), XL_WAIT_NS);
-            if (__syncthreads_or(!ok)) { failed = true; break; }
-        }
-        xl_store(sm + stg * STAGE, R, sA, sB);
-        if (ch + 1 < nch) xl_load(R, Asrc, Bsrc, m, row0, col0, (ch + 1) * XL_KC, init, ic1, ic0);
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (threadIdx.x == 0) {
+
+    if (threadIdx.x == 0) {
+        // chunk ch sits in stage ch % XL_STAGES; its copies complete phase ch / XL_STAGES of full[],
+        // its MMAs the same phase of empty[]
+        const int nch = (m + XL_KC - 1) / XL_KC;
+        auto load = [&](int ch) {
+            const int st = ch % XL_STAGES;
+            mbar_arrive_expect_tx(&full[st], XL_STAGE);
+            bulk_copy_g2s(sm + st * XL_STAGE, Apl + xl_slab(tm, ch, mp), XL_SLAB, &full[st]);
+            bulk_copy_g2s(sm + st * XL_STAGE + XL_SLAB, Bpl + xl_slab(tn, ch, mp), XL_SLAB, &full[st]);
+        };
+        int issued = 0, consumed = 0;
+        bool fail = false;
+        for (; issued < XL_STAGES && issued < nch; ++issued) load(issued);
+        for (int ch = 0; ch < nch; ++ch) {
+            const int st = ch % XL_STAGES;
+            if (!mbar_wait_bounded(&full[st], (uint32_t)((ch / XL_STAGES) & 1), XL_WAIT_NS)) {
+                fail = true;
+                break;
+            }
+            consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + stg * STAGE, ch == 0, hre, him, cre, cim);
-            mma_commit(&bar[stg]);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, hre, him, cre, cim);
+            mma_commit(&empty[st]);
+            // refill the stage of chunk ch - 1 (its MMAs were queued before these) with chunk ch - 1 + S
+            if (ch >= 1 && issued < nch) {
+                const int pc = ch - 1;
+                if (!mbar_wait_bounded(&empty[pc % XL_STAGES], (uint32_t)((pc / XL_STAGES) & 1), XL_WAIT_NS)) {
+                    fail = true;
+                    break;
+                }
+                load(issued++);
+            }
         }
+        mma_commit(&done);  // arrives once every MMA issued above has completed
+        if (fail) {
+            // copies still in flight must land before the CTA's shared memory goes away
+            for (int c = consumed; c < issued; ++c)
+                mbar_wait_bounded(&full[c % XL_STAGES], (uint32_t)((c / XL_STAGES) & 1), XL_WAIT_NS);
+        }
+        s_fail = fail;
     }
-    // every issued chunk has completed
-    if (!failed) {
-        bool ok = mbar_wait_bounded(&bar[(nch - 1) & 1], (uint32_t)(((nch - 1) >> 1) & 1), XL_WAIT_NS);
-        if (nch >= 2) ok = ok && mbar_wait_bounded(&bar[(nch - 2) & 1], (uint32_t)(((nch - 2) >> 1) & 1), XL_WAIT_NS);
-        if (__syncthreads_or(!ok)) failed = true;
-    }
-    if (!failed) {
+    __syncthreads();
+    // every thread waits for the MMAs, also after a failure (the tensor memory is freed below)
+    const bool fin = mbar_wait_bounded(&done, 0, XL_WAIT_NS);
+    if (!__syncthreads_or(!fin || s_fail)) {
         tc_fence_after();
-        // epilogue: warp w drains lanes 32 (w % 4).. (rows), columns 32 (w / 4) .. +31
-        const int quarter = warp & 3, ch0 = (warp >> 2) * 32;
-        const int r = row0 + 32 * quarter + lane;
+        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 32 (w / 4) .. + 31
+        const int quarter = warp & 3, cg = warp >> 2;
+        const int lrow = 32 * quarter + lane, r = row0 + lrow;
         const uint32_t lb = (uint32_t)(32 * quarter) << 16;
+        float2* Uo = Uout + B.u_off + (size_t)X.kw * B.mmp;
+        bool inrange = true;
         for (int g = 0; g < 4; ++g) {
-            const int cl = ch0 + 8 * g;
+            const int cl = 32 * cg + 8 * g;  // tile column of the group's first entry
             uint32_t a[8], b[8], cc[8], d[8];
             tmem_ld8_nowait(hre + lb + cl, a);
             tmem_ld8_nowait(him + lb + cl, b);
             tmem_ld8_nowait(cre + lb + cl, cc);
             tmem_ld8_nowait(cim + lb + cl, d);
             tmem_wait_ld();
-            if (r < m) {
+            float2 v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c)
+                v[c] = make_float2((__uint_as_float(a[c]) + __uint_as_float(cc[c])) * unscale,
+                                   (__uint_as_float(b[c]) + __uint_as_float(d[c])) * unscale);
+            if (mode == 1 && r < m) {
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     const int col = col0 + cl + c;
                     if (col < m) {
-                        float2 v = make_float2((__uint_as_float(a[c]) + __uint_as_float(cc[c])) * unscale,
-                                               (__uint_as_float(b[c]) + __uint_as_float(d[c])) * unscale);
-                        if (mode == 1) {
-                            const float2 x = Xm[(size_t)r * m + col];
-                            v.x = fmaf(c1, x.x, v.x) + (r == col ? c0 : 0.f);
-                            v.y = fmaf(c1, x.y, v.y);
-                        }
-                        Cdst[(size_t)r * m + col] = v;
+                        const float2 x = M.X[(size_t)r * m + col];
+                        v[c].x = fmaf(c1, x.x, v[c].x) + (r == col ? c0 : 0.f);
+                        v[c].y = fmaf(c1, x.y, v[c].y);
                     }
                 }
             }
+            if (Opl) {
+                inrange = xl_put8(Opl + xl_slab(tm, (col0 + cl) / XL_KC, mp), xl_off(lrow, cl % XL_KC), v, sout) &&
+                          inrange;
+            } else if (r < m) {
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    if (col0 + cl + c < m) Uo[(size_t)r * m + col0 + cl + c] = v[c];
+            }
         }
+        if (!inrange) atomicOr(P.status, ST_RANGE);
     } else if (threadIdx.x == 0) {
         atomicOr(P.status, ST_TIMEOUT);
-        // the commits never arrived: wait once more (bounded) before freeing the tensor memory
-        mbar_wait_bounded(&bar[0], 0, XL_WAIT_NS);
     }
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, XL_TMEM_COLS);
 }
 
-// U of every owned slice: T(X) = I + X (q = 1) or the last Horner iterate.
-__global__ void xl_export_kernel(DevPlan P, const XlItem* __restrict__ items, const float2* __restrict__ scratch,
-                                 size_t slot, float2* __restrict__ Uout) {
+// U = I + X for every owned slice of degree 1 (the GEMM chain writes U for the others).
+__global__ void xl_export_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch,
+                                 size_t xbytes, size_t pbytes, float2* __restrict__ Uout) {
     const XlItem& X = items[blockIdx.y];
-    if (!X.own) return;
+    if (!X.own || X.q >= 2) return;
     const DevBlock& B = P.blocks[X.bi];
     const int m = B.m;
     const size_t mm = (size_t)m * m;
-    const float2* base = scratch + (size_t)blockIdx.y * 4 * slot;
-    const float2* src = X.q >= 2 ? base + (size_t)(2 + ((X.q - 2) & 1)) * slot : base;
+    const float2* src = xl_mats(scratch, blockIdx.y, xbytes, pbytes).X;
     float2* Uo = Uout + B.u_off + (size_t)X.kw * B.mmp;
     for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
         float2 v = src[e];
-        if (X.q < 2) {
-            const int r = (int)(e / m), c = (int)(e - (size_t)r * m);
-            if (r == c) v.x += 1.f;
-        }
+        const int r = (int)(e / m), c = (int)(e - (size_t)r * m);
+        if (r == c) v.x += 1.f;
         Uo[e] = v;
     }
 }
 
-
 }  // namespace
 
 namespace {
-size_t xl_slot(int m_max) { return (size_t)m_max * m_max; }  // float2 entries of one matrix
-size_t xl_item_bytes(int m_max) { return 4 * xl_slot(m_max) * sizeof(float2); }
+// bytes of one slice's scratch: X in FP32, then five plane sets of the padded size
+size_t xl_xbytes(int m_max) { return ((size_t)m_max * m_max * sizeof(float2) + 1023) / 1024 * 1024; }
+size_t xl_pbytes(int m_max) { return (size_t)8 * xl_pad(m_max) * xl_pad(m_max); }
+size_t xl_item_bytes(int m_max) { return xl_xbytes(m_max) + 5 * xl_pbytes(m_max); }
 
 // slices per chunk: scratch of at most ~2 GiB, at most 256 slices, at least one
 long long xl_chunk(int m_max, long long max_items) {
@@ -399,7 +446,7 @@ long long xl_chunk(int m_max, long long max_items) {
     return std::max(1LL, std::min(c, max_items));
 }
 
-size_t xl_items_bytes(long long chunk) { return ((size_t)chunk * sizeof(XlItem) + 255) / 256 * 256; }
+size_t xl_items_bytes(long long chunk) { return ((size_t)chunk * sizeof(XlItem) + 1023) / 1024 * 1024; }
 }  // namespace
 
 int expm_large_supported(int prec, int m) { return prec != QOC_PREC_F64 && m >= 1 && m <= 2048; }
@@ -415,26 +462,29 @@ int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u,
     if (total <= 0) return 0;
     const long long ch = xl_chunk(m_max, total);
     XlItem* it = reinterpret_cast<XlItem*>(scratch);
-    float2* mats = reinterpret_cast<float2*>(scratch + xl_items_bytes(ch));
-    const size_t slot = xl_slot(m_max);
-    const int tiles = (m_max + XL_TM - 1) / XL_TM;
-    const size_t smem = (size_t)2 * 8 * XL_TM * XL_KC * 2;
+    unsigned char* mats = reinterpret_cast<unsigned char*>(scratch + xl_items_bytes(ch));
+    const size_t xb = xl_xbytes(m_max), pb = xl_pbytes(m_max);
+    const int tiles = xl_pad(m_max) / XL_TM;
+    const size_t smem = (size_t)XL_STAGES * XL_STAGE;
     if (cudaFuncSetAttribute(xl_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
     // the highest degree a slice without squarings can need (its norm is at most theta_cap)
     int qmax = 1;
     while (qmax < 16 && tabs.theta_odd[qmax - 1] < tabs.theta_cap) ++qmax;
-    const int ew_blocks = (int)std::min<size_t>(64, (slot + 255) / 256);
+    const long long groups = 2LL * xl_pad(m_max) * (xl_pad(m_max) / 8);
+    const int as_blocks = (int)std::min<long long>(64, (groups + 255) / 256);
+    const int ew_blocks = (int)std::min<size_t>(64, ((size_t)m_max * m_max + 255) / 256);
+    float2* U = reinterpret_cast<float2*>(Uout);
     for (long long i0 = 0; i0 < total; i0 += ch) {
         const int n = (int)std::min(ch, total - i0);
         xl_prep_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, tabs, u, cls, items, i0, n, it);
-        xl_assemble_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, u, it, mats, slot);
+        xl_assemble_kernel<<<dim3(as_blocks, n), 256, 0, st>>>(P, u, it, mats, xb, pb);
         if (qmax >= 2) {
-            xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, slot, tiles, 0, 0);
+            xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 0, 0, U);
             for (int j = qmax - 2; j >= 0; --j)
-                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, slot, tiles, 1, j);
+                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 1, j, U);
         }
-        xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, slot, reinterpret_cast<float2*>(Uout));
+        xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, xb, pb, U);
         if (cudaGetLastError() != cudaSuccess) return -1;
     }
     return 0;
