@@ -147,7 +147,15 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
                     ol = e - r * rn;
                     const cx<T>* row = Uk + (size_t)ol * m;
                     const cx<T>* xr = x + (size_t)r * max_m;
-                    for (int j = part; j < m; j += G) cfma<T>(acc, row[j], xr[j]);
+                    cx<T> a1 = mk<T>(0, 0);  // two chains, so that loads of successive terms overlap
+                    int j = part;
+                    for (; j + G < m; j += 2 * G) {
+                        cfma<T>(acc, row[j], xr[j]);
+                        cfma<T>(a1, row[j + G], xr[j + G]);
+                    }
+                    if (j < m) cfma<T>(acc, row[j], xr[j]);
+                    acc.x += a1.x;
+                    acc.y += a1.y;
                 }
                 for (int off = G / 2; off > 0; off >>= 1) {
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
@@ -164,7 +172,15 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
                     r = e / m;
                     o = e - r * m;
                     const cx<T>* xr = x + (size_t)r * max_m + r0 + ra;
-                    for (int ii = part; ii < rn; ii += G) cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[ii]);
+                    cx<T> a1 = mk<T>(0, 0);
+                    int ii = part;
+                    for (; ii + G < rn; ii += 2 * G) {
+                        cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[ii]);
+                        cfma_conj<T>(a1, Uk[(size_t)(ii + G) * m + o], xr[ii + G]);
+                    }
+                    if (ii < rn) cfma_conj<T>(acc, Uk[(size_t)ii * m + o], xr[ii]);
+                    acc.x += a1.x;
+                    acc.y += a1.y;
                 }
                 for (int off = G / 2; off > 0; off >>= 1) {
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, off);
