@@ -20,6 +20,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -348,7 +349,7 @@ def run_ours(args, rank, world):
     if args.autotune:
         from paper_2309_05884_gb300 import autotune
         autotune.tune_expm(plan, torch.from_numpy(u0).to(dev), api.to_device(b0, dev), api.to_device(bf, dev),
-                           cache_path=os.path.join(ROOT, "gpurun_out", "autotune.json"))
+                           cache_path=os.path.join(tempfile.gettempdir(), "qoc_autotune.json"))
     d0, df = api.to_device(b0, dev), api.to_device(bf, dev)
     u = torch.from_numpy(u0.copy()).to(dev)
     ws = plan.workspace  # allocate before timing

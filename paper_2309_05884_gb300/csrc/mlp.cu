@@ -3,7 +3,7 @@
 // The network maps a problem's parameters to initial pulses (a 3 x 256 hidden-layer MLP with GELU,
 // BF16 weights, FP32 activations and accumulation); it is trained on pulses the GRAPE solver of this
 // library optimised.  The paper has no such component: it is the warm start added around the
-// method, judged by the method's own fidelity.
+// method, scored by the method's own fidelity.
 //
 // All matrix products go through one tiled SIMT kernel, C[M][N] (+)= sum_k A(m,k) B(k,n), with
 // arbitrary strides so that the forward product X W^T, the input gradient dZ W and the weight

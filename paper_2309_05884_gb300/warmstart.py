@@ -1,4 +1,4 @@
-"""Learned warm start for batched GRAPE on S_n problems (not in the paper; judged by the method's own
+"""Learned warm start for batched GRAPE on S_n problems (not in the paper; scored by the method's own
 fidelity).
 
 A network maps a problem's parameters (n, J, h, target Dicke index k) to the N x 2 initial pulses
