@@ -28,11 +28,9 @@ def _fd_check(plan, u, b0, bf):
     plan.sync_status()
     g = g.cpu().numpy()
     N, nc = u.shape
-    rng = np.random.default_rng(FD_SEED)
-    picks = rng.choice(N * nc, size=min(N_ENTRIES, N * nc), replace=False)
+    picks = I.fd_entries(FD_SEED, N, nc, N_ENTRIES)
     fd = np.empty(len(picks))
-    for i, e in enumerate(picks):
-        k, j = divmod(int(e), nc)
+    for i, (k, j) in enumerate(picks):
         vals = []
         for sgn in (1.0, -1.0):
             up = u.copy()
@@ -41,7 +39,7 @@ def _fd_check(plan, u, b0, bf):
             torch.cuda.synchronize()
             vals.append(o[0].item())
         fd[i] = (vals[0] - vals[1]) / (2 * H_FD)
-    sel = np.array([g[divmod(int(e), nc)] for e in picks])
+    sel = np.array([g[k, j] for k, j in picks])
     assert np.abs(sel).max() > 1e-3  # a gradient well above the FD rounding floor
     rel = np.linalg.norm(fd - sel) / np.linalg.norm(sel)
     assert rel <= 1e-6, rel
