@@ -64,6 +64,15 @@ def ising_ring(n: int, Bz: float, c_cpl: float, T: float, N: int) -> System:
     return System(n, group, h0, hc, T, N, name=f"ising_ring_n{n}")
 
 
+def ising_ring_full(n: int, Bz: float, c_cpl: List[float], T: float, N: int) -> System:
+    """Eq. H0MoreCoupling1: H0 = Bz/2 sum Z + sum_{d=1..floor(n/2)} c^(d)/4 sum_i Z_i Z_{i+d} (every
+    ring distance, taken literally, so d = n/2 counts each pair twice for even n); Hc as in Eq. Hc."""
+    assert len(c_cpl) == n // 2
+    h0 = [(SUM_Z, 0.5 * Bz, 0)] + [(RING_ZZ, 0.25 * c, d + 1) for d, c in enumerate(c_cpl) if c != 0.0]
+    hc = [[(SUM_X, 0.5, 0)], [(SUM_Y, 0.5, 0)]]
+    return System(n, GROUP_DN, h0, hc, T, N, name=f"ising_ring_full_n{n}")
+
+
 def sn_allpairs(n: int, J: float, h: float, T: float, N: int) -> System:
     """S_n-invariant H0 = J sum_{i<j} Z_i Z_j + h sum Z_i; controls u_x sum X, u_y sum Y."""
     return System(n, GROUP_SN, [(ALLPAIRS_ZZ, J, 0), (SUM_Z, h, 0)],

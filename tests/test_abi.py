@@ -57,8 +57,9 @@ def _oracle_blocks(system):
 
 
 @pytest.mark.parametrize("system", [I.c1_system(), I.xxz_ring(6, 1.0, 10), I.xxz_ring(8, 1.0, 10),
-                                    I.ising_ring(7, 1.0, 0.6, 1.0, 10), I.sn_allpairs(6, 0.7, 0.3, 1.0, 10)],
-                         ids=["c1", "xxz6", "xxz8", "ising7", "sn6"])
+                                    I.ising_ring(7, 1.0, 0.6, 1.0, 10), I.sn_allpairs(6, 0.7, 0.3, 1.0, 10),
+                                    I.ising_ring_full(8, 1.0, [0.8, 0.37, 0.23, 0.11], 1.0, 10)],
+                         ids=["c1", "xxz6", "xxz8", "ising7", "sn6", "ising8_full"])
 def test_host_blocks_match_oracle(system):
     from oracle import symmetry as sy
     from paper_2309_05884_gb300 import api
@@ -126,3 +127,19 @@ def test_dicke_state_in_block_coordinates():
         assert np.abs(B.blocks_to_state(blk) - op.dicke_state(6, k)).max() < 1e-12
     big = api.Basis(I.sn_allpairs(40, 1.0, 0.5, 1.0, 10))
     assert big.n_blocks == 1 and big.state_len == 41
+
+
+def test_host_first_block_resonances_full_coupling():
+    # Sec. III / Fig. 4d on the library's own blocks: n = 4, nearest-neighbour coupling gives three
+    # resonance frequencies in the first subspace, the full coupling of Eq. H0MoreCoupling1 six
+    from paper_2309_05884_gb300 import api
+
+    def resonances(s):
+        B = api.Basis(s, first_block_only=True)
+        h0, hc = B.block_matrices(0)
+        w, Q = np.linalg.eigh(h0)
+        X = Q.conj().T @ hc[0] @ Q
+        return {round(abs(w[a] - w[b]), 9) for a in range(len(w)) for b in range(a) if abs(X[a, b]) > 1e-9}
+
+    assert len(resonances(I.ising_ring(4, 1.0, 0.8, 1.0, 1))) == 3
+    assert len(resonances(I.ising_ring_full(4, 1.0, [0.8, 0.37], 1.0, 1))) == 6

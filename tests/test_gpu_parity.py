@@ -267,3 +267,18 @@ def test_fp32_dn_ragged_sizes():
     # n = 9: blocks of 14..58 (one to four 16-row tiles, ragged tails)
     s = I.xxz_ring(9, 3.0, 60)
     check(s, I.random_state(110, 512), I.random_state(111, 512), I.pulses_normal(9, s.N, 3), "f32", TOL32)
+
+
+def test_ising_ring_full_coupling_fp64():
+    # Eq. H0MoreCoupling1 (every ring distance up to floor(n/2)), |up^n> to a seeded target in the
+    # first D_n block (Sec. II.B), and up^n -> down^n
+    s = I.ising_ring_full(8, 1.0, [0.8, 0.37, 0.23, 0.11], 6.0, 60)
+    _, psif = a1_target(s, 112)
+    F, _ = check(s, I.basis_state(8, 0), psif, I.pulses_uniform(6, 60, 2), "f64", TOL64)
+    assert F > 1e-3
+    check(s, I.basis_state(8, 0), I.basis_state(8, 255), I.pulses_uniform(6, 60, 2), "f64", TOL64)
+
+
+def test_ising_ring_full_coupling_fp32_all_blocks():
+    s = I.ising_ring_full(9, 1.0, [0.8, 0.37, 0.23, 0.11], 2.0, 40)
+    check(s, I.random_state(90, 512), I.random_state(91, 512), I.pulses_uniform(7, 40, 2), "f32", TOL32)

@@ -87,8 +87,9 @@ def test_dn_unitary_and_block_diagonal(n):
     blocks = sy.dn_blocks(n)
     A = sy.adjoint_matrix(blocks)
     assert np.abs(A.conj().T @ A - np.eye(2 ** n)).max() < 1e-12
-    kinds = [(I.SUM_X, 0), (I.SUM_Y, 0), (I.SUM_Z, 0), (I.RING_ZZ, 1), (I.RING_XX, 1),
-             (I.RING_YY, 1), (I.RING_ZZ, 2)]
+    # every ring distance of Eq. H0MoreCoupling1 keeps the D_n blocks
+    kinds = [(I.SUM_X, 0), (I.SUM_Y, 0), (I.SUM_Z, 0), (I.RING_XX, 1), (I.RING_YY, 1)] + \
+        [(I.RING_ZZ, d) for d in range(1, n // 2 + 1)]
     for kind, d in kinds:
         X = op.term_matrix(n, kind, d).toarray()
         off, B = _offblock_norm(blocks, X)
@@ -141,3 +142,31 @@ def test_round_trip_blocks():
     psi = I.random_state(5, 2 ** n)
     c = sy.to_blocks(blocks, psi)
     assert np.abs(sy.from_blocks(blocks, c) - psi).max() < 1e-12
+
+
+def _first_block_resonances(s):
+    """Distinct transition energies |E_a - E_b| between eigenstates of H0 in the first D_n block that
+    the control sum X connects (the resonance frequencies of Sec. III)."""
+    H0, Hc = op.system_operators(s)
+    _, V = sy.symmetry_blocks(s)[0]
+    w, Q = np.linalg.eigh(sy.block_operator(V[0], H0))
+    X = Q.conj().T @ sy.block_operator(V[0], Hc[0]) @ Q
+    return len(w), {round(abs(w[a] - w[b]), 9) for a in range(len(w)) for b in range(a) if abs(X[a, b]) > 1e-9}
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6])
+def test_resonances_nearest_neighbour_vs_full_coupling(n):
+    # Sec. III: with the nearest-neighbour coupling of Eq. H0WithCoupling the first subspace has three
+    # resonance frequencies for every n >= 3; the full coupling of Eq. H0MoreCoupling1 breaks the
+    # degeneracy, giving six for n = 4 (Fig. 4d); for n = 3 the two forms coincide (floor(n/2) = 1)
+    m, nn = _first_block_resonances(I.ising_ring(n, 1.0, 0.8, 1.0, 1))
+    assert m == {3: 4, 4: 6, 5: 8, 6: 13}[n]  # Table I
+    assert len(nn) == 3
+    couplings = [0.8, 0.37, 0.23][: n // 2]
+    _, full = _first_block_resonances(I.ising_ring_full(n, 1.0, couplings, 1.0, 1))
+    if n == 3:
+        assert full == nn
+    else:
+        assert len(full) > len(nn)
+    if n == 4:
+        assert len(full) == 6
