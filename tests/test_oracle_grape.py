@@ -127,7 +127,11 @@ def test_gradient_fd_large_norm_slices():
     _fd_check(prob, I.pulses_uniform(4, s.N, 2), s.tau, seed=5, tol=2e-6)
 
 
-@pytest.mark.parametrize("system_fn,seed", [(I.c1_system, 0), (lambda: I.xxz_ring(6, 4.0, 40), 2)])
+@pytest.mark.parametrize("system_fn,seed", [
+    (I.c1_system, 0), (lambda: I.xxz_ring(6, 4.0, 40), 2),
+    (lambda: I.ising_ring_full(8, 1.0, [0.8, 0.37, 0.23, 0.11], 3.0, 12), 4),
+    pytest.param(lambda: I.xxz_ring(10, 1.0, 4), 6, marks=pytest.mark.slow)],
+    ids=["c1", "xxz6", "ising8_full", "xxz10"])
 def test_full_space_equals_block_space(system_fn, seed):
     s = system_fn()
     dim = 2 ** s.n
