@@ -18,7 +18,10 @@ The paper's own derivative (Eq. propagator_differentiation) keeps only the first
 
 Pins (tests/test_oracle_grape.py): single-qubit and collective Rabi closed forms, detuned Rabi,
 sigma_x^{(x)n} transfer, unitarity, the analytic diagonal case, central finite differences, the
-first-order limit, and full-space == block-space trajectories.
+first-order limit, and full-space == block-space trajectories.  The gate objective at the end of
+this file (trace fidelity of Sec. IV against a target gate) is pinned in tests/test_oracle_gate.py:
+tensor-power closed forms, full space == block form with copy multiplicities, the maximum at the
+reached gate, and central differences of the plain trace.
 """
 from __future__ import annotations
 
@@ -202,3 +205,47 @@ def grape(problem, u0: np.ndarray, tau: float, iters: int, step: float, f_target
             return u, hist, it
         u = u + step * g
     return u, hist, iters
+
+
+# ------------------------------------------------------------------------------------------------
+# Gate (unitary) objective.  Sec. IV compares two propagators K, K' of the full space by the trace
+# fidelity F = |Tr(K^dagger K') / 2^n|^2; as a control objective the target is a gate W and
+# K' = U_N ... U_1.  With a symmetric W (one that commutes with the group, e.g. U_sq^{(x)n}, Sec.
+# III) both are block diagonal in the adapted basis, every copy of block b carries the same block,
+# and the full-space trace is the sum over blocks of mult_b Tr(W_b^dagger U_b).
+# ------------------------------------------------------------------------------------------------
+def gate_overlap(blocks, W_blocks, mult, u: np.ndarray, tau: float) -> complex:
+    """g = sum_b mult_b Tr(W_b^dagger U_bN ... U_b1) / d with d = sum_b mult_b m_b; the plain product
+    of the propagators, block by block."""
+    d = sum(c * np.asarray(W).shape[0] for W, c in zip(W_blocks, mult))
+    g = 0.0 + 0.0j
+    for blk, W, c in zip(blocks, W_blocks, mult):
+        K = np.eye(np.asarray(W).shape[0], dtype=np.complex128)
+        for U in propagators(blk, u, tau):
+            K = U @ K
+        g += c * np.trace(np.conj(np.asarray(W, dtype=np.complex128)).T @ K)
+    return complex(g / d)
+
+
+def gate_fidelity(blocks, W_blocks, mult, u: np.ndarray, tau: float) -> float:
+    """F = |Tr(W^dagger U) / d|^2 (the trace fidelity of Sec. IV with the gate as the target)."""
+    return abs(gate_overlap(blocks, W_blocks, mult, u, tau)) ** 2
+
+
+def gate_problem(blocks, W_blocks, mult):
+    """The gate objective as a state-transfer problem: in block b the identity columns, weighted by
+    sqrt(mult_b / d), are carried to the target's columns W_b e_r with the same weight, so that
+    sum_b sum_r <psif_br|psi_N,br> = sum_b (mult_b / d) Tr(W_b^dagger U_b) = g.  The exact gradient
+    of F then follows from fidelity_and_grad's costate formula with m columns per block."""
+    d = sum(c * np.asarray(W).shape[0] for W, c in zip(W_blocks, mult))
+    out = []
+    for blk, W, c in zip(blocks, W_blocks, mult):
+        W = np.asarray(W, dtype=np.complex128)
+        s = np.sqrt(c / d)
+        out.append(dict(h0=blk["h0"], hc=blk["hc"], psi0=s * np.eye(W.shape[0], dtype=np.complex128), psif=s * W))
+    return out
+
+
+def gate_fidelity_and_grad(blocks, W_blocks, mult, u: np.ndarray, tau: float):
+    """(F, g, dF/du [N, nc]) of the gate objective with the exact slice derivative."""
+    return fidelity_and_grad(gate_problem(blocks, W_blocks, mult), u, tau)
