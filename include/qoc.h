@@ -254,15 +254,14 @@ int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
  * products as in qoc_tc_cgemm), param 0 = only the slices that need no squaring (the block's other
  * slices run on the tiled kernel in a second launch), param 1 = every slice; kind 3 = tcgen05 tiled
  * batched GEMMs for large blocks (FP32 plans, m <= 2048; 128 x 128 output tiles, one launch per
- * product over a chunk of slices) for the slices that need no squaring, the tiled kernel for the
- * rest (param ignored).  Blocks no rule covers
- * use the tiled kernel.  At plan creation QOC_PREC_F32 plans use kind 2, param 0 for blocks of
- * 25..112 states, kind 3 for 113..2048 and the tiled kernel for the rest; QOC_PREC_F32_ALL and FP64
- * plans use the tiled kernel.  A tensor-core product
- * (two FP16 halves per operand, all four split products) errs up to about 2x an FP32 one, which
- * the squarings of large-norm slices would amplify.   The plan's
- * workspace size may change: query qoc_plan_workspace_bytes again.  An autotuner times candidate
- * rules (paper_2309_05884_gb300/autotune.py). */
+ * product over a chunk of slices, operands kept in the workspace as pre-split FP16 planes) for the
+ * slices that need no squaring, the tiled kernel for the rest (param ignored).  Blocks no rule
+ * covers use the tiled kernel.  At plan creation QOC_PREC_F32 plans use kind 2, param 0 for blocks
+ * of 25..112 states, kind 3 for 113..2048 and the tiled kernel for the rest; QOC_PREC_F32_ALL and
+ * FP64 plans use the tiled kernel.  A tensor-core product (two FP16 halves per operand, all four
+ * split products) errs up to about 2x an FP32 one, which the squarings of large-norm slices would
+ * amplify.  The plan's workspace size may change: query qoc_plan_workspace_bytes again.  An
+ * autotuner times candidate rules (paper_2309_05884_gb300/autotune.py). */
 int qoc_plan_set_expm_rules(qoc_plan* plan, int n_rules, const int* m_max, const int* kind, const int* param);
 /* The plan's current exponential launches: kind, param (R or MP), matrices per warp, largest block
  * and block count of each; arrays of max_out entries (may be NULL). */
