@@ -10,7 +10,10 @@ Modules
               dimensions by characters, block Hamiltonians A^dagger H A
 - grape     : piecewise-constant propagation (Eq. exppropagator), state-transfer fidelity
               (Eq. probability), exact and first-order (Eq. propagator_differentiation)
-              gradients, finite differences, gradient ascent
+              gradients, finite differences, gradient ascent; the gate (trace) fidelity objective
+- trotter   : the Trotterised propagator for per-qubit controls and its transformed form (Sec. IV,
+              Eqs. propagator_cpl, propagator_cpl_transformed), trace fidelity of propagators
+- mlp       : the warm-start network's forward and backward pass
 
 Every function is pinned by a test in tests/ against values the paper prints (Table I) or
 against closed forms and invariants; see each module's header.
