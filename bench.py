@@ -285,7 +285,7 @@ class D14:
         return 0  # the checkpointed passes time sweeps together with the exponentials
 
     def cpu_rate(self):
-        Ns = 2
+        Ns = 4  # about 15 s of oracle work on 16 host cores
         rate, secs = cpu_oracle_rate(self._s, self._p0, self._pf, self._u, Ns)
         return rate, (f"one FP64 oracle F + exact gradient over the first {Ns} of {self._s.N} slices "
                       f"(all blocks, numpy/BLAS default threads; block set-up not timed), {secs:.1f} s, "
