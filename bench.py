@@ -332,6 +332,23 @@ def run_warmstart(args, rank, world):
 WORKLOADS = {"d10": D10, "d14": D14, "sn-batch": SnBatch, "warmstart": None}
 
 
+# --------------------------------------------------------------------------- replicas
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest x over all ranks (every rank gets it); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, problems: int, steps: int, total_ms: float) -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * problems * steps / (total_ms / 1e3)
+
+
 # --------------------------------------------------------------------------- GPU leg
 def run_ours(args, rank, world):
     import torch
@@ -388,13 +405,8 @@ def run_ours(args, rank, world):
     counts = plan.work_counts()
     plan.set_profiling(False)
     plan.sync_status()
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * wl.problems * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(float(np.sum(step_ms)), world, dev)
+    value = job_rate(world, wl.problems, args.steps, total_ms)
     ph = np.mean(np.array(phases), axis=0)
 
     # rooflines per phase, from algorithmic work per call (complex multiply-add = 8 flop) and the
