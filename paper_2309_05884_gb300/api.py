@@ -7,7 +7,7 @@ interleaved (re, im) double layout of the C ABI).
 from __future__ import annotations
 
 import ctypes as C
-from typing import List, Optional, Sequence, Tuple
+from typing import List, Optional, Tuple
 
 import numpy as np
 import torch
