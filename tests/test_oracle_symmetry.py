@@ -154,19 +154,31 @@ def _first_block_resonances(s):
     return len(w), {round(abs(w[a] - w[b]), 9) for a in range(len(w)) for b in range(a) if abs(X[a, b]) > 1e-9}
 
 
+def _golden_resonances():
+    path = os.path.join(os.path.dirname(__file__), "golden", "resonances.txt")
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if line.strip() and not line.startswith("#"):
+                kind, n, count = line.split()
+                out[(kind, int(n))] = int(count)
+    return out
+
+
 @pytest.mark.parametrize("n", [3, 4, 5, 6])
 def test_resonances_nearest_neighbour_vs_full_coupling(n):
     # Sec. III: with the nearest-neighbour coupling of Eq. H0WithCoupling the first subspace has three
     # resonance frequencies for every n >= 3; the full coupling of Eq. H0MoreCoupling1 breaks the
     # degeneracy, giving six for n = 4 (Fig. 4d); for n = 3 the two forms coincide (floor(n/2) = 1)
+    gold = _golden_resonances()
     m, nn = _first_block_resonances(I.ising_ring(n, 1.0, 0.8, 1.0, 1))
     assert m == {3: 4, 4: 6, 5: 8, 6: 13}[n]  # Table I
-    assert len(nn) == 3
+    assert len(nn) == gold[("nn", n)]
     couplings = [0.8, 0.37, 0.23][: n // 2]
     _, full = _first_block_resonances(I.ising_ring_full(n, 1.0, couplings, 1.0, 1))
     if n == 3:
         assert full == nn
     else:
         assert len(full) > len(nn)
-    if n == 4:
-        assert len(full) == 6
+    if ("full", n) in gold:
+        assert len(full) == gold[("full", n)]
