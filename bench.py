@@ -439,6 +439,11 @@ def run_ours(args, rank, world):
                                  "real FP16 products per complex product on padded operands"
                                  + ("; checkpointed: timed over the forward pass (exponentials + forward "
                                     "sweep), a lower bound for the exponentials alone" if ckpt else "")}
+        # the split does 4 real FP16 products per real product, so a kernel that kept the tensor pipe
+        # busy all the time would reach a quarter of the peak in these algorithmic units
+        roofs["expm"]["split_ceiling"] = {
+            "peak": tc_peak / 4, "frac": roofs["expm"]["achieved"] / (tc_peak / 4),
+            "note": "algorithmic rate of a split-FP16 kernel with the tensor pipe always busy"}
     else:
         roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles)",
                          "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
