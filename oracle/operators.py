@@ -5,8 +5,10 @@ the leftmost (most significant) Kronecker factor; H_x, H_y, H_z are sums over qu
 coupling sum_i sigma^(i) sigma^(i+1) is periodic (sigma^(n+i) = sigma^(i)).  Eq.
 H0MoreCoupling1 extends the ring coupling to distance d.
 
-Pins: tests/test_oracle_operators.py (Pauli algebra, Hermiticity, ring/all-pairs counting,
-single-qubit Rabi closed form through grape.py).
+Pins: tests/test_oracle_operators.py (Pauli algebra; the XXZ ring's one-magnon spectrum
+4 cos(2 pi k d / n) + Delta (n - 4) on the full space and per D_n irrep; exact Z-ring values at every
+distance d <= n/2; the all-pairs Heisenberg coupling as 2 J (J + 1) - 3 n / 2; collective-field
+spectra) and tests/test_oracle_grape.py (Rabi closed forms).
 """
 from __future__ import annotations
 
