@@ -23,8 +23,12 @@
  *     block Hamiltonians they hold.
  *   - Stream arguments are cudaStream_t passed as void* (NULL = legacy default stream).  Calls that
  *     take a stream are asynchronous on it; argument errors are returned synchronously before any
- *     launch.  Kernel-side errors (a NaN pulse, an exhausted iteration cap) are latched in a device
- *     status word of the plan and returned by qoc_plan_sync_status().
+ *     launch.  Kernel-side errors (a NaN pulse, an initial or target state whose norm is not 1, an
+ *     exhausted iteration cap, a bounded wait that gave up) are latched in a device status word of
+ *     the plan.  Every call on the plan ends by queueing a copy of that word to pinned host memory;
+ *     the next call that starts after that copy has completed on the GPU returns the latched error
+ *     (and clears it) before it launches anything.  qoc_plan_sync_status() waits and returns it at
+ *     once.  No call waits for the GPU to find out (inside a stream capture neither step runs).
  *
  * Every function returns QOC_OK (0) or a negative error code; qoc_last_error() gives a message for
  * the calling thread's last failure.
@@ -42,7 +46,7 @@ extern "C" {
 /* ---------------------------------------------------------------- error codes */
 enum {
     QOC_OK = 0,
-    QOC_EINVAL = -1,          /* bad argument, shape, NaN/Inf input, unnormalised state */
+    QOC_EINVAL = -1,          /* bad argument, shape, NaN/Inf input, unnormalised state (|norm - 1| > 1e-8) */
     QOC_ENOMEM = -2,          /* host or device allocation failed, or workspace too small */
     QOC_ECUDA = -3,           /* a CUDA runtime call failed */
     QOC_ETIMEOUT = -4,        /* a bounded device wait gave up */
@@ -180,6 +184,14 @@ int qoc_plan_workspace_bytes(const qoc_plan* plan, size_t* bytes);
 /* Return and clear the plan's device status word (synchronises the given stream). */
 int qoc_plan_sync_status(qoc_plan* plan, void* stream);
 
+/* Failure-path self-test of the bounded waits (no counterpart in the paper): launches one kernel
+ * that waits on a shared-memory mbarrier that nothing completes, with the same bounded-wait routine
+ * the propagator and sweep kernels use on their bulk copies and tensor-core commits.  The wait gives
+ * up after limit_ms (0.001..1000) and latches the timeout bit, so that qoc_plan_sync_status (or the
+ * next call on the plan, once this one has finished) returns QOC_ETIMEOUT; the context stays usable.
+ * Asynchronous on stream. */
+int qoc_plan_selftest_wait(qoc_plan* plan, double limit_ms, void* stream);
+
 /* Block assembly (Eq. exppropagator's exponent): A_out[b][k] = -i dt (H0_b + sum_j u_kj Hc_jb) for
  * every active block b and slice k, as m_b*m_b complex128 row-major matrices packed block-major
  * (block b at complex offset N * sum_{b'<b} m_b'^2).
@@ -200,10 +212,28 @@ int qoc_propagate(const qoc_plan* plan, const double* u, const double* psi0, dou
  *   out3 (dev, 3 doubles per problem) = { F, Re o, Im o },  o = sum over the problem's active copies
  *   <psif|psi_N>,  F = |o|^2
  *   grad (dev [N][n_ctrl], may be NULL) = dF/du_kj = 2 Re(conj(o) sum lam_k^dagger dU_k/du_kj psi_{k-1})
- * psi0, psif: dev block states (state_len complex128). */
+ * psi0, psif: dev block states (state_len complex128), each of norm 1 per problem (checked on the
+ * device to 1e-8: QOC_EINVAL, latched).  The forward states and the costates run concurrently. */
 int qoc_fidelity_and_grad(const qoc_plan* plan, const double* u, const double* psi0,
                           const double* psif, double* out3, double* grad, void* workspace,
                           size_t workspace_bytes, void* stream);
+
+/* The same computation in two halves, for reverse-mode differentiation (a framework's backward runs
+ * only when a gradient is asked for):
+ *   qoc_fidelity_forward: propagators, forward states psi_k = U_k psi_{k-1} (Eq. exppropagator) and
+ *     out3 as above.  The workspace keeps the states of every slice (with checkpointing: of every
+ *     segment boundary), the propagators (without checkpointing) and the overlaps o_p.
+ *   qoc_fidelity_backward: costates lam_N = psif, lam_{k-1} = U_k^dagger lam_k (Appendix B), the exact
+ *     slice derivatives (with checkpointing each segment's propagators and states are recomputed, as
+ *     in qoc_fidelity_and_grad) and grad[k][j] = gF_p * dF_p/du_kj for the rows of problem p;
+ *     gF: dev [n_problems] doubles (a caller's dL/dF_p), NULL for 1.
+ * qoc_fidelity_backward needs the workspace exactly as the last qoc_fidelity_forward on the same
+ * plan left it (same u, psif; no other call on that workspace in between); the library cannot check
+ * this. */
+int qoc_fidelity_forward(const qoc_plan* plan, const double* u, const double* psi0, const double* psif,
+                         double* out3, void* workspace, size_t workspace_bytes, void* stream);
+int qoc_fidelity_backward(const qoc_plan* plan, const double* u, const double* psif, const double* gF,
+                          double* grad, void* workspace, size_t workspace_bytes, void* stream);
 
 /* Gradient ascent (GRAPE, Sec. II.A) on every problem of the plan. */
 enum { QOC_RULE_FIXED = 0,   /* u <- u + step * dF/du */
@@ -226,6 +256,10 @@ void qoc_opt_opts_default(qoc_opt_opts* opts);
 
 /* For it = 0..iters-1: F and dF/du of every problem, F_hist[it][p] = F_p (dev, iters*n_problems
  * doubles), then the update of u (dev [rows][n_ctrl], in place) unless problem p is frozen.
+ * The initial pulses are u as the caller passes it: a warm start is the caller writing proposed
+ * pulses (for instance the warm-start network's output, qoc_dense_forward) into u first, and a
+ * fallback is a second call on the problems that did not converge, from other pulses.
+ * Every convergence check also reads the status word: a latched error ends the loop with its code.
  * reached (dev, n_problems ints, may be NULL): first iteration whose F_p >= f_target, -1 if none.
  * *iters_done (host, may be NULL) receives the iterations run.  Returns QOC_ENOTCONVERGED if
  * f_target <= 1 and some problem did not reach it. */
@@ -324,7 +358,8 @@ int qoc_to_bf16(const float* x, uint16_t* y, long long n, void* stream);
  * that loads libqoc.so keeps until the process exits.
  *   - m must be 1..128, else QOC_EUNSUPPORTED with a message; count >= 0 (0 is a no-op).
  *   - The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- *     that device current; make that first call before any stream capture starts.
+ *     that device current; make that first call before any stream capture starts.  If the device
+ *     is reset (cudaDeviceReset) the next call finds the cached address stale and looks it up again.
  *   - All calls share the array: calls whose kernels overlap on the GPU (other streams, other host
  *     threads) race and return wrong results; serialise them.
  *   - Asynchronous on 'stream'; errors of the launch itself are returned. */

@@ -75,6 +75,9 @@ SIGNATURES = {
     "qoc_expm_blocks": (C.c_int, [P, P, P, P, C.c_size_t, P]),
     "qoc_propagate": (C.c_int, [P, P, P, P, P, C.c_size_t, P]),
     "qoc_fidelity_and_grad": (C.c_int, [P, P, P, P, P, P, P, C.c_size_t, P]),
+    "qoc_fidelity_forward": (C.c_int, [P, P, P, P, P, P, C.c_size_t, P]),
+    "qoc_fidelity_backward": (C.c_int, [P, P, P, P, P, P, C.c_size_t, P]),
+    "qoc_plan_selftest_wait": (C.c_int, [P, C.c_double, P]),
     "qoc_opt_opts_default": (None, [C.POINTER(qoc_opt_opts)]),
     "qoc_optimize_pulses": (C.c_int, [P, P, P, P, C.POINTER(qoc_opt_opts), P, P, C.POINTER(C.c_int), P,
                                       C.c_size_t, P]),

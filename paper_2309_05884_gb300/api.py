@@ -152,6 +152,7 @@ class Plan:
         self._ws = None
         self._graph_stream = None
         self.last_reached = None
+        self._fwd_serial = 0  # counts forward halves; a backward half must follow its own forward
 
     def __del__(self):
         if getattr(self, "handle", None):
@@ -190,6 +191,43 @@ class Plan:
                                                _ptr(grad) if want_grad else None, _ptr(ws), ws.numel(),
                                                _stream(stream)), "qoc_fidelity_and_grad")
         return out3, (grad if want_grad else None)
+
+    def forward(self, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, out3: Optional[torch.Tensor] = None,
+                stream=None) -> Tuple[torch.Tensor, int]:
+        """Forward half (qoc_fidelity_forward): out3 = [F, Re o, Im o] per problem and a serial number
+        that backward() must be given; the workspace keeps the states backward() needs."""
+        self._check_u(u)
+        self._check_state(psi0)
+        self._check_state(psif)
+        if out3 is None:
+            out3 = torch.empty(3 * self.n_prob, dtype=torch.float64, device=u.device)
+        ws = self.workspace
+        L.check(self.lib.qoc_fidelity_forward(self.handle, _ptr(u), _ptr(psi0), _ptr(psif), _ptr(out3), _ptr(ws),
+                                              ws.numel(), _stream(stream)), "qoc_fidelity_forward")
+        self._fwd_serial += 1
+        return out3, self._fwd_serial
+
+    def backward(self, u: torch.Tensor, psif: torch.Tensor, serial: int, gF: Optional[torch.Tensor] = None,
+                 grad: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        """Backward half (qoc_fidelity_backward): grad = gF_p dF_p/du from the workspace that the forward
+        half numbered 'serial' left; raises if another forward half ran on this plan since."""
+        if serial != self._fwd_serial:
+            raise RuntimeError("the plan's workspace was reused by a later forward pass; run forward again")
+        self._check_u(u)
+        self._check_state(psif)
+        if grad is None:
+            grad = torch.empty_like(u)
+        if gF is not None:
+            assert gF.dtype == torch.float64 and gF.is_cuda and gF.is_contiguous() and gF.numel() == self.n_prob
+        ws = self.workspace
+        L.check(self.lib.qoc_fidelity_backward(self.handle, _ptr(u), _ptr(psif), _ptr(gF), _ptr(grad), _ptr(ws),
+                                               ws.numel(), _stream(stream)), "qoc_fidelity_backward")
+        return grad
+
+    def selftest_wait(self, limit_ms: float = 1.0, stream=None) -> None:
+        """Launch a bounded wait that nothing completes (qoc_plan_selftest_wait); sync_status() then
+        raises QOC_ETIMEOUT."""
+        L.check(self.lib.qoc_plan_selftest_wait(self.handle, float(limit_ms), _stream(stream)), "qoc_plan_selftest_wait")
 
     def propagate(self, u: torch.Tensor, psi0: torch.Tensor, psiN: Optional[torch.Tensor] = None, stream=None):
         self._check_u(u)
@@ -328,19 +366,28 @@ class Plan:
 
 
 class FidelityGrad(torch.autograd.Function):
-    """F(u) = |<psi_f|psi_N(u)>|^2 with its hand-written adjoint (costate sweep + exact slice
-    derivatives): forward runs the whole hot path once and keeps dF/du for backward."""
+    """F(u) = |<psi_f|psi_N(u)>|^2 (one problem: a scalar; a batch plan: [n_prob]) with its
+    hand-written adjoint.  forward runs the propagators, the forward states (kept per slice, or at
+    checkpoints) and the overlap; backward runs the costate sweep and the exact slice derivatives
+    (recomputing checkpointed segments) and scales dF_p/du by the incoming dL/dF_p on the device.
+    Under torch.no_grad, or when no gradient is asked for, no costate kernel runs."""
 
     @staticmethod
     def forward(ctx, u: torch.Tensor, plan: Plan, psi0: torch.Tensor, psif: torch.Tensor):
-        out3, g = plan.fidelity_and_grad(u.detach().contiguous(), psi0, psif, want_grad=True)
-        ctx.save_for_backward(g)
-        return out3[0].clone()
+        uc = u.detach().contiguous()
+        out3, serial = plan.forward(uc, psi0, psif)
+        ctx.plan, ctx.u, ctx.psif, ctx.serial = plan, uc, psif, serial
+        F = out3.view(plan.n_prob, 3)[:, 0].clone()
+        return F[0] if plan.n_prob == 1 else F
 
     @staticmethod
     def backward(ctx, gF):
-        (g,) = ctx.saved_tensors
-        return gF * g, None, None, None
+        plan = ctx.plan
+        gFd = gF.detach().to(torch.float64).reshape(-1).contiguous()
+        if gFd.numel() == 1 and plan.n_prob > 1:
+            gFd = gFd.expand(plan.n_prob).contiguous()
+        g = plan.backward(ctx.u, ctx.psif, ctx.serial, gF=gFd)
+        return g, None, None, None
 
 
 def to_device(blk: np.ndarray, device=None) -> torch.Tensor:

@@ -44,6 +44,7 @@ enum : int {
     ST_SERIES_CAP = 4,      // a slice's gradient series did not reach its tolerance
     ST_TIMEOUT = 8,         // a bounded wait on an asynchronous copy gave up
     ST_RANGE = 16,          // a tensor-core operand left the range of its FP16 split
+    ST_NORM = 32,           // an initial or target block state whose norm is not 1
 };
 
 // Per-active-block table, in device memory (one entry per active block of every problem).
@@ -76,6 +77,8 @@ struct UpdateRule {
     double* adam_m;   // [rows][nc] first moments
     double* adam_v;   // [rows][nc] second moments
     double* F_hist;   // [iters][n_prob] or null
+    const double* gscale;  // [n_prob] factors applied to problem p's gradient (chain rule of a
+                           // caller's dL/dF_p), or null for 1
 };
 
 // Everything a kernel needs about the plan, passed by value.

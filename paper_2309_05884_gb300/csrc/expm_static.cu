@@ -16,7 +16,9 @@
 // Host code may not use the array's name as a device address: on the host it names a stand-in
 // object, and a kernel handed that pointer would fault or touch the wrong memory.  The device
 // address is looked up once per device with cudaGetSymbolAddress (with that device current) on
-// the first call made on it; make that first call before any stream capture begins.
+// the first call made on it; make that first call before any stream capture begins.  Later calls
+// check that the cached address is still device memory of the current device (a cudaDeviceReset
+// tears the module down with its context) and look it up again if not.
 #include <mutex>
 #include <string>
 
@@ -34,6 +36,7 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[QOC_NOALLOC_SCR
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_dev_ptr[kMaxDevices] = {};
+bool g_theta_ready = false;
 
 __constant__ int c_sp[9] = {2, 2, 3, 3, 4, 4, 5, 5, 5};
 __constant__ int c_sq[9] = {1, 2, 2, 3, 3, 4, 4, 5, 6};
@@ -145,6 +148,18 @@ double theta64(int d) {
     return lo;
 }
 
+Theta g_theta;
+
+// The cached address is still this device's memory (false after a device reset, for instance).
+bool still_valid(void* ptr, int dev) {
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
+}
+
 }  // namespace
 }  // namespace qoc
 
@@ -164,6 +179,12 @@ extern "C" int qoc_expm_batch_noalloc(const double* A, double* U, int m, long lo
     void* ptr = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_mu);
+        if (!g_theta_ready) {
+            const int degs[9] = {2, 4, 6, 9, 12, 16, 20, 25, 30};
+            for (int i = 0; i < 9; ++i) g_theta.t[i] = theta64(degs[i]);
+            g_theta_ready = true;
+        }
+        if (g_dev_ptr[dev] && !still_valid(g_dev_ptr[dev], dev)) g_dev_ptr[dev] = nullptr;
         if (!g_dev_ptr[dev]) {
             // first call on this device: look up the device address of the module's array
             e = cudaGetSymbolAddress(&g_dev_ptr[dev], g_noalloc_scratch);
@@ -177,9 +198,7 @@ extern "C" int qoc_expm_batch_noalloc(const double* A, double* U, int m, long lo
     const size_t slot = ((size_t)10 * m * m * sizeof(double2) + 255) / 256 * 256;
     const long long slots = (long long)(QOC_NOALLOC_SCRATCH_BYTES / slot);
     const int grid = (int)(count < slots ? count : slots);
-    Theta th;
-    const int degs[9] = {2, 4, 6, 9, 12, 16, 20, 25, 30};
-    for (int i = 0; i < 9; ++i) th.t[i] = theta64(degs[i]);
+    const Theta th = g_theta;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double2* a = reinterpret_cast<const double2*>(A);
     double2* u = reinterpret_cast<double2*>(U);

@@ -362,7 +362,7 @@ __global__ void grad_reduce_kernel(DevPlan P, const double2* __restrict__ partia
             sr += d.x;
             si += d.y;
         }
-        const double gv = 2.0 * (o.x * sr + o.y * si);
+        const double gv = 2.0 * (o.x * sr + o.y * si) * (rule.gscale ? rule.gscale[p] : 1.0);
         const size_t idx = (size_t)row0 * nc + e;
         if (grad) grad[idx] = gv;
         if (u && rule.kind >= 0 && !frozen) {

@@ -80,6 +80,13 @@ int launch_gather(const DevPlan& P, const double2* src, void* dst, cudaStream_t 
 // o = sum_{active copies} <psif | psi_N> (FP64) with psi_N in boundary layout; out3 = {|o|^2, Re o, Im o}.
 int launch_overlap(const DevPlan& P, const void* fin, const double2* psif, double* out3, double2* o_ws,
                    cudaStream_t st);
+// Per problem p (prob_state[2p] = complex offset, [2p+1] = length of its block state): latch ST_NORM
+// when | ||a_p|| - 1 | or | ||b_p|| - 1 | (b may be null) exceeds tol, FP64 sums.
+int launch_norm_check(const int64_t* prob_state, int n_prob, const double2* a, const double2* b, double tol,
+                      int* status, cudaStream_t st);
+// A bounded wait on an mbarrier that nothing completes: gives up after limit_ns and latches
+// ST_TIMEOUT, the path every bounded wait of the kernels takes when a copy or commit never lands.
+int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t st);
 // psiN (caller's block state, complex128) <- fin (boundary layout); inactive copies are zeroed.
 int launch_store_final(const DevPlan& P, const void* fin, double2* psiN, long long state_len, cudaStream_t st);
 

@@ -105,6 +105,10 @@ struct qoc_plan {
     int* d_prob_blocks = nullptr;
     int* d_prob_block_off = nullptr;
     int* d_status = nullptr;
+    int64_t* d_prob_state = nullptr;  // [n_prob][2]: complex offset and length of each problem's block state
+    int* h_status = nullptr;          // pinned host copy of d_status, written at the end of every call
+    cudaEvent_t st_ev = nullptr;      // recorded after that copy
+    mutable bool st_recorded = false;
     unsigned long long* d_stats = nullptr;
     bool profiling = false;
     bool capturing = false;
@@ -176,6 +180,65 @@ int check_ws(const qoc_plan* p, void* ws, size_t bytes) {
     if (bytes < p->ws_bytes)
         return set_error(QOC_ENOMEM, "workspace too small: need " + std::to_string(p->ws_bytes) + " bytes");
     if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return set_error(QOC_EINVAL, "workspace must be 256-byte aligned");
+    return QOC_OK;
+}
+
+// The error code of a set of latched status bits (the most severe first).
+int status_error(int st) {
+    if (st & ST_TIMEOUT) return set_error(QOC_ETIMEOUT, "a bounded device wait gave up");
+    if (st & ST_NAN_PULSE) return set_error(QOC_EINVAL, "non-finite pulse value");
+    if (st & ST_NORM)
+        return set_error(QOC_EINVAL, "an initial or target block state has a norm that differs from 1 by more than 1e-8");
+    if (st & ST_SQUARING_CAP) return set_error(QOC_EUNSUPPORTED, "a slice needed more squarings than max_squarings");
+    if (st & ST_SERIES_CAP) return set_error(QOC_EUNSUPPORTED, "a slice's norm is beyond the gradient series' range");
+    if (st & ST_RANGE)
+        return set_error(QOC_EUNSUPPORTED, "a tensor-core expm operand left the FP16-split range (non-Hermitian H?)");
+    return QOC_OK;
+}
+
+bool stream_capturing(cudaStream_t st) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return false;
+    }
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Status bits latched by earlier calls on the plan whose work has finished on the GPU: returned (and
+// cleared) at the start of the next call.  Bits of calls still running are left for a later call or
+// for qoc_plan_sync_status; nothing here waits for the GPU.
+int take_latched(const qoc_plan* p, cudaStream_t st) {
+    if (!p->st_recorded || p->capturing || stream_capturing(st)) return QOC_OK;
+    const cudaError_t q = cudaEventQuery(p->st_ev);
+    if (q == cudaErrorNotReady) {
+        (void)cudaGetLastError();
+        return QOC_OK;
+    }
+    if (q != cudaSuccess) return cuda_fail(q, "status event");
+    const int bits = *reinterpret_cast<volatile int*>(p->h_status);
+    p->st_recorded = false;
+    if (!bits) return QOC_OK;
+    *reinterpret_cast<volatile int*>(p->h_status) = 0;
+    cudaMemsetAsync(p->d_status, 0, sizeof(int), st);
+    return status_error(bits);
+}
+
+// Queue the copy of the status word that the next call reads (not inside a stream capture).
+void record_status(const qoc_plan* p, cudaStream_t st) {
+    if (p->capturing || stream_capturing(st)) return;
+    if (cudaMemcpyAsync(p->h_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st) == cudaSuccess &&
+        cudaEventRecord(p->st_ev, st) == cudaSuccess)
+        p->st_recorded = true;
+    else
+        (void)cudaGetLastError();
+}
+
+// Norms of the caller's initial (and target, may be null) block states, checked on the device.
+int check_norms(const qoc_plan* p, const double* a, const double* b, cudaStream_t st) {
+    if (launch_norm_check(p->d_prob_state, p->n_prob, reinterpret_cast<const double2*>(a),
+                          reinterpret_cast<const double2*>(b), 1e-8, p->d_status, st) != 0)
+        return cuda_fail(cudaGetLastError(), "norm check launch");
     return QOC_OK;
 }
 
@@ -460,6 +523,63 @@ int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, c
     return QOC_OK;
 }
 
+// The forward half of fidelity_grad_impl: propagators, forward states (every slice, or the segment
+// boundaries when checkpointing) and the overlaps; the workspace keeps what backward_impl needs.
+int forward_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3, char* w,
+                 cudaStream_t st) {
+    int rc;
+    auto mark = [&](int i) {
+        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
+    };
+    mark(0);
+    if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
+    mark(1);
+    mark(2);
+    if (launch_overlap(p->dev(), ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3,
+                       reinterpret_cast<double2*>(w + p->off_o), st) != 0)
+        return cuda_fail(cudaGetLastError(), "overlap launch");
+    mark(3);
+    return QOC_OK;
+}
+
+// The backward half: costates from lam_N = psi_f, exact slice derivatives (recomputing each segment's
+// propagators and states when checkpointing) and grad = gF_p dF_p/du.
+int backward_impl(const qoc_plan* p, const double* u, const double* psif, const double* gF, double* grad, char* w,
+                  cudaStream_t st) {
+    int rc;
+    auto mark = [&](int i) {
+        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
+    };
+    const DevPlan P = p->dev();
+    if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
+        return cuda_fail(cudaGetLastError(), "gather launch");
+    if (p->nseg == 1) {
+        if ((rc = run_sweeps(p, w, 0, -1, 2, nullptr, nullptr, lamb_vec(p, w, 0), lamb_vec(p, w, 1), st))) return rc;
+        if ((rc = run_grad(p, u, w, 0, -1, st))) return rc;
+    } else {
+        int cur = 0;
+        for (int s = p->nseg - 1; s >= 0; --s) {
+            int k0, nk;
+            window_of(p, s, &k0, &nk);
+            if ((rc = run_expm(p, u, w, k0, nk, st))) return rc;
+            if ((rc = run_sweeps(p, w, k0, nk, 3, ckpt_vec(p, w, s), ckpt_vec(p, w, s + 1), lamb_vec(p, w, cur),
+                                 lamb_vec(p, w, cur ^ 1), st)))
+                return rc;
+            if ((rc = run_grad(p, u, w, k0, nk, st))) return rc;
+            cur ^= 1;
+        }
+    }
+    mark(4);
+    UpdateRule rule = no_update();
+    rule.gscale = gF;
+    if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial),
+                           reinterpret_cast<const double2*>(w + p->off_o), grad, nullptr, rule,
+                           reinterpret_cast<const double*>(w + p->off_out3), st) != 0)
+        return cuda_fail(cudaGetLastError(), "reduce launch");
+    mark(5);
+    return QOC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -695,11 +815,24 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     QOC_UP(p->d_prob_blocks, p->prob_blocks.data(), p->prob_blocks.size(), "upload problems");
     QOC_UP(p->d_prob_block_off, p->prob_block_off.data(), p->prob_block_off.size(), "upload problems");
     QOC_UP(p->d_H64, reinterpret_cast<double2*>(H64.data()), H64.size(), "upload H");
-#undef QOC_UP
+    {
+        std::vector<int64_t> ps;
+        for (const auto& pr : p->probs) {
+            ps.push_back(pr.state_off);
+            ps.push_back(pr.basis->state_len);
+        }
+        QOC_UP(p->d_prob_state, ps.data(), ps.size(), "upload problems");
+    }
     if ((e = cudaMalloc(&p->d_status, sizeof(int))) != cudaSuccess) return fail(e, "cudaMalloc status");
+    if ((e = cudaHostAlloc(&p->h_status, sizeof(int), cudaHostAllocDefault)) != cudaSuccess)
+        return fail(e, "cudaHostAlloc status");
+    *p->h_status = 0;
+    if ((e = cudaEventCreateWithFlags(&p->st_ev, cudaEventDisableTiming)) != cudaSuccess)
+        return fail(e, "cudaEventCreate");
     if ((e = cudaMalloc(&p->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc stats");
     cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
     cudaMemset(p->d_status, 0, sizeof(int));
+#undef QOC_UP
     for (auto& ev : p->ev)
         if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e, "cudaEventCreate");
     if (o.prec == QOC_PREC_F64) {
@@ -739,6 +872,9 @@ void qoc_plan_free(qoc_plan* p) {
     cudaFree(p->d_prob_blocks);
     cudaFree(p->d_prob_block_off);
     cudaFree(p->d_status);
+    cudaFree(p->d_prob_state);
+    if (p->h_status) cudaFreeHost(p->h_status);
+    if (p->st_ev) cudaEventDestroy(p->st_ev);
     cudaFree(p->d_stats);
     for (auto& ev : p->ev)
         if (ev) cudaEventDestroy(ev);
@@ -769,12 +905,19 @@ int qoc_plan_sync_status(qoc_plan* p, void* stream) {
     e = cudaMemcpy(&st, p->d_status, sizeof(int), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "status read");
     cudaMemset(p->d_status, 0, sizeof(int));
-    if (st & ST_TIMEOUT) return set_error(QOC_ETIMEOUT, "a bounded device wait gave up");
-    if (st & ST_NAN_PULSE) return set_error(QOC_EINVAL, "non-finite pulse value");
-    if (st & ST_SQUARING_CAP) return set_error(QOC_EUNSUPPORTED, "a slice needed more squarings than max_squarings");
-    if (st & ST_SERIES_CAP) return set_error(QOC_EUNSUPPORTED, "a slice's norm is beyond the gradient series' range");
-    if (st & ST_RANGE)
-        return set_error(QOC_EUNSUPPORTED, "a tensor-core expm operand left the FP16-split range (non-Hermitian H?)");
+    *reinterpret_cast<volatile int*>(p->h_status) = 0;
+    p->st_recorded = false;
+    return status_error(st);
+}
+
+int qoc_plan_selftest_wait(qoc_plan* p, double limit_ms, void* stream) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    if (!(limit_ms >= 0.001 && limit_ms <= 1000.0)) return set_error(QOC_EINVAL, "limit_ms must be in [0.001, 1000]");
+    cudaSetDevice(p->device);
+    cudaStream_t st = to_stream(stream);
+    if (launch_wait_selftest((unsigned long long)(limit_ms * 1e6), p->d_status, st) != 0)
+        return cuda_fail(cudaGetLastError(), "self-test launch");
+    record_status(p, st);
     return QOC_OK;
 }
 
@@ -910,10 +1053,12 @@ int qoc_expm_blocks(const qoc_plan* p, const double* u, double* U_out, void* ws,
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
+    if ((rc = take_latched(p, st))) return rc;
     if (p->nseg == 1) {
         if ((rc = run_expm(p, u, w, 0, -1, st))) return rc;
         if (launch_export_u(p->dev(), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
             return cuda_fail(cudaGetLastError(), "export launch");
+        record_status(p, st);
         return QOC_OK;
     }
     for (int s = 0; s < p->nseg; ++s) {
@@ -923,6 +1068,7 @@ int qoc_expm_blocks(const qoc_plan* p, const double* u, double* U_out, void* ws,
         if (launch_export_u(p->dev(k0, nk), w + p->off_U, reinterpret_cast<double2*>(U_out), p->d_a_off, st) != 0)
             return cuda_fail(cudaGetLastError(), "export launch");
     }
+    record_status(p, st);
     return QOC_OK;
 }
 
@@ -934,9 +1080,12 @@ int qoc_propagate(const qoc_plan* p, const double* u, const double* psi0, double
     cudaSetDevice(p->device);
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
+    if ((rc = take_latched(p, st))) return rc;
+    if ((rc = check_norms(p, psi0, nullptr, st))) return rc;
     if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
     if (launch_store_final(p->dev(), ckpt_vec(p, w, p->nseg), reinterpret_cast<double2*>(psiN), p->state_len, st) != 0)
         return cuda_fail(cudaGetLastError(), "store launch");
+    record_status(p, st);
     return QOC_OK;
 }
 
@@ -946,8 +1095,39 @@ int qoc_fidelity_and_grad(const qoc_plan* p, const double* u, const double* psi0
     int rc = check_ws(p, ws, ws_bytes);
     if (rc) return rc;
     cudaSetDevice(p->device);
-    return fidelity_grad_impl(p, u, psi0, psif, out3, grad, nullptr, no_update(), static_cast<char*>(ws),
-                              to_stream(stream));
+    cudaStream_t st = to_stream(stream);
+    if ((rc = take_latched(p, st))) return rc;
+    if ((rc = check_norms(p, psi0, psif, st))) return rc;
+    rc = fidelity_grad_impl(p, u, psi0, psif, out3, grad, nullptr, no_update(), static_cast<char*>(ws), st);
+    if (rc == QOC_OK) record_status(p, st);
+    return rc;
+}
+
+int qoc_fidelity_forward(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3,
+                         void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !u || !psi0 || !psif || !out3) return set_error(QOC_EINVAL, "null argument");
+    int rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    cudaSetDevice(p->device);
+    cudaStream_t st = to_stream(stream);
+    if ((rc = take_latched(p, st))) return rc;
+    if ((rc = check_norms(p, psi0, psif, st))) return rc;
+    rc = forward_impl(p, u, psi0, psif, out3, static_cast<char*>(ws), st);
+    if (rc == QOC_OK) record_status(p, st);
+    return rc;
+}
+
+int qoc_fidelity_backward(const qoc_plan* p, const double* u, const double* psif, const double* gF, double* grad,
+                          void* ws, size_t ws_bytes, void* stream) {
+    if (!p || !u || !psif || !grad) return set_error(QOC_EINVAL, "null argument");
+    int rc = check_ws(p, ws, ws_bytes);
+    if (rc) return rc;
+    cudaSetDevice(p->device);
+    cudaStream_t st = to_stream(stream);
+    if ((rc = take_latched(p, st))) return rc;
+    rc = backward_impl(p, u, psif, gF, grad, static_cast<char*>(ws), st);
+    if (rc == QOC_OK) record_status(p, st);
+    return rc;
 }
 
 void qoc_opt_opts_default(qoc_opt_opts* o) {
@@ -978,6 +1158,8 @@ int qoc_optimize_pulses(qoc_plan* p, double* u, const double* psi0, const double
     char* w = static_cast<char*>(ws);
     cudaStream_t st = to_stream(stream);
     if (o.use_graph && st == nullptr) return set_error(QOC_EINVAL, "graph replay needs a non-default stream");
+    if ((rc = take_latched(p, st))) return rc;
+    if ((rc = check_norms(p, psi0, psif, st))) return rc;
     double* out3 = reinterpret_cast<double*>(w + p->off_out3);
     int* d_iter = reinterpret_cast<int*>(w + p->off_iter);
     int* d_reached = reached ? reached : reinterpret_cast<int*>(w + p->off_reached);
@@ -1002,10 +1184,19 @@ int qoc_optimize_pulses(qoc_plan* p, double* u, const double* psi0, const double
     const bool stop_early = o.f_target <= 1.0;
     const int check_every = o.check_every < 1 ? 1 : o.check_every;
     std::vector<int> h_reached(p->n_prob);
+    // every convergence check also reads the status word: a latched error ends the optimisation
     auto all_reached = [&](bool* all) -> int {
         cudaError_t e = cudaMemcpyAsync(h_reached.data(), d_reached, sizeof(int) * p->n_prob, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(p->h_status, p->d_status, sizeof(int), cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "convergence read");
+        const int bits = *reinterpret_cast<volatile int*>(p->h_status);
+        if (bits) {
+            *reinterpret_cast<volatile int*>(p->h_status) = 0;
+            p->st_recorded = false;
+            cudaMemsetAsync(p->d_status, 0, sizeof(int), st);
+            return status_error(bits);
+        }
         *all = true;
         for (int v : h_reached)
             if (v < 0) *all = false;
@@ -1065,6 +1256,7 @@ int qoc_optimize_pulses(qoc_plan* p, double* u, const double* psi0, const double
         if ((rc = all_reached(&all))) return rc;
         if (!all) return set_error(QOC_ENOTCONVERGED, "F_target not reached by every problem");
     }
+    record_status(p, st);
     return QOC_OK;
 }
 

@@ -194,6 +194,50 @@ __global__ void store_final_kernel(DevPlan P, const cx<T>* __restrict__ fin, dou
     }
 }
 
+// One CTA per problem: FP64 norms of its initial and target block states (every copy, active or
+// not: the caller's whole state); latches ST_NORM if either is off 1 by more than tol (or not finite).
+__global__ void __launch_bounds__(256)
+norm_check_kernel(const int64_t* __restrict__ prob_state, const double2* __restrict__ a,
+                  const double2* __restrict__ b, double tol, int* status) {
+    __shared__ double sa[256], sb[256];
+    const int p = blockIdx.x;
+    const int64_t off = prob_state[2 * p], len = prob_state[2 * p + 1];
+    double na = 0.0, nb = 0.0;
+    for (int64_t e = threadIdx.x; e < len; e += blockDim.x) {
+        const double2 x = a[off + e];
+        na = fma(x.x, x.x, fma(x.y, x.y, na));
+        if (b) {
+            const double2 y = b[off + e];
+            nb = fma(y.x, y.x, fma(y.y, y.y, nb));
+        }
+    }
+    sa[threadIdx.x] = na;
+    sb[threadIdx.x] = nb;
+    __syncthreads();
+    for (int s = 128; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            sa[threadIdx.x] += sa[threadIdx.x + s];
+            sb[threadIdx.x] += sb[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const bool ok_a = fabs(sqrt(sa[0]) - 1.0) <= tol;
+        const bool ok_b = !b || fabs(sqrt(sb[0]) - 1.0) <= tol;
+        if (!(ok_a && ok_b)) atomicOr(status, ST_NORM);
+    }
+}
+
+// Nothing arrives on the barrier, so its phase 0 never completes: the bounded wait gives up.
+__global__ void wait_selftest_kernel(unsigned long long limit_ns, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_mbar_init();
+        if (!mbar_wait_bounded(&bar, 0, limit_ns)) atomicOr(status, ST_TIMEOUT);
+    }
+}
+
 template <class T>
 size_t sweep_smem(int m, int c, int staged, long long mmp) {
     return (staged ? 2 * (size_t)mmp * sizeof(cx<T>) : 0) + 2 * (size_t)m * c * sizeof(cx<T>);
@@ -224,6 +268,17 @@ int launch_sweeps(const DevPlan& P, const void* U, const void* fwd_init, void* f
             P, (const float2*)U, (const float2*)fwd_init, (float2*)fwd_out, (const float2*)bwd_init,
             (float2*)bwd_out, (float2*)psi_store, (float2*)lam_store, dirs, staged);
     }
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_norm_check(const int64_t* prob_state, int n_prob, const double2* a, const double2* b, double tol,
+                      int* status, cudaStream_t st) {
+    norm_check_kernel<<<n_prob, 256, 0, st>>>(prob_state, a, b, tol, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
+}
+
+int launch_wait_selftest(unsigned long long limit_ns, int* status, cudaStream_t st) {
+    wait_selftest_kernel<<<1, 32, 0, st>>>(limit_ns, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

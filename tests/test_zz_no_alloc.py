@@ -64,3 +64,29 @@ def test_noalloc_larger_blocks_and_limits():
     # sizes beyond the fixed array's limit are rejected before any launch
     rc = lib.qoc_expm_batch_noalloc(C.c_void_p(A.data_ptr()), C.c_void_p(U.data_ptr()), 129, 1, None)
     assert rc == _lib.QOC_EUNSUPPORTED and b"1..128" in lib.qoc_last_error()
+
+
+def test_noalloc_largest_size_persistent_slots():
+    # m = 128, the largest size the fixed array takes: six slots of 10 m^2 complex, so 13 matrices make
+    # the CTAs loop over the batch; one matrix has a large norm (squarings).  Reference: the
+    # eigendecomposition of each Hermitian H, U = V exp(-i tau w) V^dagger.
+    lib = _lib.load()
+    m, count, tau = 128, 13, 0.05
+    g = I.rng(77)
+    Hs = []
+    for i in range(count):
+        X = g.normal(size=(m, m)) + 1j * g.normal(size=(m, m))
+        H = (X + X.conj().T) / 2 * (40.0 if i == 5 else 1.0)
+        Hs.append(H)
+    A = np.stack([-1j * tau * H for H in Hs])
+    ref = []
+    for H in Hs:
+        w, V = np.linalg.eigh(H)
+        ref.append((V * np.exp(-1j * tau * w)) @ V.conj().T)
+    At = torch.from_numpy(A).to(DEV)
+    for _ in range(2):   # two calls in a row on the shared array
+        U = torch.zeros_like(At)
+        rc = lib.qoc_expm_batch_noalloc(C.c_void_p(At.data_ptr()), C.c_void_p(U.data_ptr()), m, count, None)
+        assert rc == _lib.QOC_OK, lib.qoc_last_error()
+        torch.cuda.synchronize()
+        assert np.abs(U.cpu().numpy() - np.stack(ref)).max() <= 1e-10
