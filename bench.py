@@ -1,17 +1,21 @@
-"""Benchmark: GRAPE gradient evaluations per second on the D_10 XXZ ring workload.
+"""Benchmark: GRAPE gradient evaluations per second on the largest single-GPU workload, the D_14 XXZ
+ring with sqrt(N) checkpointing.
 
-Workload (default): n = 10 qubits, H0 = sum_i (X_i X_{i+1} + Y_i Y_{i+1} + 0.5 Z_i Z_{i+1}) on a
-periodic ring, controls u_x sum X, u_y sum Y, u_z sum Z, T = 20, N = 500 slices, pulses ~ N(0, 0.3^2)
-(seed 1).  All eight D_10 irrep blocks (A1 78, A2 30, B1 58, B2 42, E1 99 x2, E2 105 x2, E3 99 x2,
-E4 105 x2) carry amplitude: the initial and target states are seeded random full-space states, so
-every block is propagated.  Complex FP32 Taylor polynomial and sweeps, FP64 squaring chain, overlap
-and gradient accumulation.  One step = one GRAPE iteration: F, dF/du (exact slice derivatives) and
-the update u <- u + eps dF/du, all on the device.
+Workload (default, --workload d14): n = 14 qubits, H0 = sum_i (X_i X_{i+1} + Y_i Y_{i+1} + 0.5 Z_i
+Z_{i+1}) on a periodic ring, controls u_x sum X, u_y sum Y, u_z sum Z, T = 40, N = 2000 slices,
+pulses ~ N(0, 0.3^2) (seed 1).  All ten D_14 irrep blocks (A1 687, A2 495, B1 613, B2 549, E1-E6
+1161/1179 x2 copies) carry amplitude: the initial and target states are seeded random full-space
+states.  sqrt(N) checkpointing (45-slice segments): the costate pass recomputes each segment's
+propagators.  Complex FP32 Taylor polynomial (tcgen05 tensor cores for blocks of 25..2048 states)
+and sweeps, FP64 squaring chain, overlap and gradient accumulation.  One step = one GRAPE iteration:
+F, dF/du (exact slice derivatives) and the update u <- u + eps dF/du, all on the device.
+Other workloads: d10 (n = 10, T = 20, N = 500, every propagator stored), sn-batch (256 batched S_n
+problems), warmstart (time to F >= 0.999 with and without the learned warm start).
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--workload ...]
 
 Prints one JSON line.  --impl reference times the FP64 CPU oracle on a bounded sample of the same
-workload (the first 50 slices per step, scaled to whole gradient evaluations).
+workload (a few slices per step, scaled to whole gradient evaluations).
 """
 from __future__ import annotations
 
@@ -42,18 +46,33 @@ FP32_PEAK_NOTE = "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max S
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
-def measured_peaks():
-    """HBM and dense tensor peaks from MEASURED_PEAKS.json (the profiling recipe's fallback if absent)."""
+def measured_peaks(long_step: bool = False):
+    """HBM and dense tensor peaks from MEASURED_PEAKS.json (the profiling recipe's fallback if absent).
+    long_step: the kernel runs inside a step of seconds, so the sustained tensor rate applies."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "hbm_note": "measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
-                "tensor_tflops": float(d["bf16_tflops"]),
-                "tensor_note": "measured dense BF16 burst rate (MEASURED_PEAKS.json bf16_tflops); FP16 x 1"}
+        key = "bf16_tflops_sustained" if long_step and "bf16_tflops_sustained" in d else "bf16_tflops"
+        how = "sustained" if key.endswith("sustained") else "burst"
+        return {"hbm_gbs": float(d["hbm_gbs"]), "hbm_note": "of measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)",
+                "tensor_tflops": float(d[key]),
+                "tensor_note": f"of measured dense BF16 {how} rate (MEASURED_PEAKS.json {key}); FP16 x 1"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "hbm_note": "fallback 6.8 TB/s", "tensor_tflops": 1900.0,
-                "tensor_note": "fallback 1.9 PFLOP/s BF16 burst; FP16 x 1"}
+        t = 1700.0 if long_step else 1900.0
+        return {"hbm_gbs": 6800.0, "hbm_note": "of fallback 6.8 TB/s", "tensor_tflops": t,
+                "tensor_note": f"of fallback {t / 1000:.1f} PFLOP/s BF16; FP16 x 1"}
+
+
+# DRAM bytes (read + write) of one launch of a workload's dominant kernel, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum), with the launch it was taken on and that launch's
+# algorithmic bytes; None where the kernel changed after the capture.  The profiles/ summaries
+# name the commands.
+NCU_TRAFFIC = {
+    "d14": {"kernel": "xl_gemm_kernel", "bytes": 735.6e6 + 340.1e6, "algorithmic_bytes": 734e6 + 367e6,
+            "launch": "first product of the first chunk: 28 slices of the m = 1179 block, 100 tiles each",
+            "source": "profiles/xl_gemm_kernel_d14.md"},
+}
 
 
 def workload():
@@ -161,9 +180,13 @@ def cpu_oracle_rate(s, psi0, psif, u, N_sample, reps=1):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    s, psi0, psif, u = workload()
+    if args.workload == "d14":
+        s, psi0, psif, u = d14_workload()
+        Ns, name = 2, D14_WORKLOAD
+    else:
+        s, psi0, psif, u = workload()
+        Ns, name = 50, WORKLOAD
     from oracle import grape as gr
-    Ns = 50
     sub, prob = oracle_problem(s, psi0, psif, Ns)
     uu = u[:Ns].copy()
     for _ in range(args.warmup):
@@ -182,7 +205,7 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD},
+        "data": "synthetic", "config": {"workload": name},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }), flush=True)
@@ -195,6 +218,8 @@ class D10:
     problems = 1
     prec = "f32"
     step_kw = dict(step=EPS, rule="fixed")
+    key = "d10"
+    default_steps = 300
 
     def build(self, api, dev):
         s, psi0_full, psif_full, u0 = workload()
@@ -221,6 +246,8 @@ class SnBatch:
     problems = SN_BATCH
     prec = "f32_all"
     step_kw = dict(step=0.02, rule="fixed")
+    key = "sn-batch"
+    default_steps = 20
 
     def build(self, api, dev):
         probs = sn_batch_problems()
@@ -262,6 +289,14 @@ D14_WORKLOAD = (f"D_14 XXZ ring (n=14, T={D14_T:g}, N={D14_N}, 3 controls), seed
                 "checkpoint segments (45 slices), the costate pass recomputes each segment")
 
 
+def d14_workload():
+    s = I.xxz_ring(14, D14_T, D14_N)
+    psi0 = I.random_state(SEED_PSI0, 2 ** s.n)
+    psif = I.random_state(SEED_PSIF, 2 ** s.n)
+    u0 = I.pulses_normal(SEED_U, s.N, s.n_ctrl)
+    return s, psi0, psif, u0
+
+
 class D14:
     """The D_14 XXZ ring with sqrt(N) checkpointing (adjoint + recomputation)."""
     name = D14_WORKLOAD
@@ -269,12 +304,13 @@ class D14:
     prec = "f32"
     step_kw = dict(step=EPS, rule="fixed")
     ckpt = True
+    key = "d14"
+    default_steps = 4
+    e2e_steps = 2
+    long_step = True   # a step of seconds: the sustained tensor peak applies
 
     def build(self, api, dev):
-        s = I.xxz_ring(14, D14_T, D14_N)
-        psi0 = I.random_state(SEED_PSI0, 2 ** s.n)
-        psif = I.random_state(SEED_PSIF, 2 ** s.n)
-        u0 = I.pulses_normal(SEED_U, s.N, s.n_ctrl)
+        s, psi0, psif, u0 = d14_workload()
         B = api.Basis(s)
         b0, bf = B.state_to_blocks(psi0), B.state_to_blocks(psif)
         plan = api.Plan(B, s.N, s.tau, prec=self.prec, active=B.active_copies(b0, bf), ckpt_segment=-1)
@@ -358,6 +394,8 @@ def run_ours(args, rank, world):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     wl = WORKLOADS[args.workload]()
+    if args.prec != "default":
+        wl.prec = args.prec
     plan, u0, b0, bf = wl.build(api, dev)
     if args.expm_kernel == "tc":
         plan.set_expm_rules([(112, 2, 0)])      # tcgen05 tensor cores where the block fits
@@ -410,21 +448,16 @@ def run_ours(args, rank, world):
     ph = np.mean(np.array(phases), axis=0)
 
     # rooflines per phase, from algorithmic work per call (complex multiply-add = 8 flop) and the
-    # in-step CUDA-event phase times; the line's "roofline" is the phase that takes longest
-    peaks = measured_peaks()
+    # in-step CUDA-event phase times (each the sum of that phase's launch durations on the launching
+    # stream); the line's "roofline" is the phase that takes longest
+    peaks = measured_peaks(getattr(wl, "long_step", False))
     n = args.steps
     phase_ms = {"expm": float(ph[0]), "sweeps": float(ph[1]), "overlap": float(ph[2]),
                 "slice_derivatives": float(ph[3]), "reduce_update": float(ph[4])}
     classes = plan.expm_classes()
     kinds = {c[0] for c in classes}
     ckpt = getattr(wl, "ckpt", False)
-    expm_flop = 8.0 * (counts[0] + counts[1]) / n
-    if ckpt:
-        # [0]..[1] is the forward pass (every slice's exponential + the forward sweep); the costate
-        # pass repeats the exponentials, so half of the counted products fall in the forward pass
-        expm_flop /= 2
-        phase_ms = {"expm": phase_ms["expm"], "overlap": phase_ms["overlap"],
-                    "costate_pass": phase_ms["slice_derivatives"], "reduce_update": phase_ms["reduce_update"]}
+    expm_flop = 8.0 * (counts[0] + counts[1]) / n   # both passes when checkpointing
     roofs = {}
     if kinds & {2, 3}:
         # kind::f16 MMAs: the measured BF16 dense rate (FP16 has the same nominal rate)
@@ -434,11 +467,12 @@ def run_ours(args, rank, world):
         roofs["expm"] = {"bound": "tensor", "kernel": kern,
                          "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": tc_peak,
                          "unit": "TFLOP/s", "peak_source": tc_src,
-                         "flops_per_launch": expm_flop,
-                         "note": "algorithmic complex-FP32 flop (8 m^3 per product); the split issues 16 "
-                                 "real FP16 products per complex product on padded operands"
-                                 + ("; checkpointed: timed over the forward pass (exponentials + forward "
-                                    "sweep), a lower bound for the exponentials alone" if ckpt else "")}
+                         "flops_per_step": expm_flop,
+                         "note": "algorithmic complex-FP32 flop (8 m^3 per product) over the summed durations of "
+                                 "the exponential launches; the split issues 16 real FP16 products per complex "
+                                 "product on padded operands"
+                                 + ("; checkpointed: every exponential is computed twice (forward pass and "
+                                    "costate pass), both counted" if ckpt else "")}
         # the split does 4 real FP16 products per real product, so a kernel that kept the tensor pipe
         # busy all the time would reach a quarter of the peak in these algorithmic units
         roofs["expm"]["split_ceiling"] = {
@@ -447,23 +481,27 @@ def run_ours(args, rank, world):
     else:
         roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles)",
                          "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_launch": expm_flop}
+                         "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_step": expm_flop}
     grad_flop = 8.0 * counts[3] / n
-    if grad_flop > 0 and not ckpt:
+    if grad_flop > 0:
         roofs["slice_derivatives"] = {
             "bound": "alu", "kernel": "grad_fast_kernel (register tiles, FP32 FMA)",
             "achieved": grad_flop / (phase_ms["slice_derivatives"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-            "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_launch": grad_flop,
+            "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_step": grad_flop,
             "note": "series work (c (3P+1) + n_ctrl) m^2 complex multiply-adds per (slice, block) item"}
     sweep_bytes = wl.sweep_bytes(plan)
     if sweep_bytes:
         roofs["sweeps"] = {"bound": "hbm", "kernel": "sweep_cluster_kernel" if plan.sweep_cluster() else "sweep_kernel",
                            "achieved": sweep_bytes / (phase_ms["sweeps"] * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                           "unit": "GB/s", "peak_source": peaks["hbm_note"], "bytes_per_launch": sweep_bytes,
+                           "unit": "GB/s", "peak_source": peaks["hbm_note"], "bytes_per_step": sweep_bytes,
                            "note": "every stored propagator read once forward and once backward"}
     for r in roofs.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["traffic"] = None
+    tr = NCU_TRAFFIC.get(getattr(wl, "key", ""))
+    if tr and "expm" in roofs and roofs["expm"]["kernel"].startswith(tr["kernel"]):
+        roofs["expm"]["traffic"] = tr["bytes"]
+        roofs["expm"]["traffic_launch"] = {k: tr[k] for k in ("launch", "algorithmic_bytes", "source")}
     dominant = max((k for k in roofs), key=lambda k: phase_ms[k])
     roof = dict(roofs[dominant])
     roof["phase"] = dominant
@@ -478,7 +516,7 @@ def run_ours(args, rank, world):
     u_d, d0e, dfe = torch.empty_like(u), torch.empty_like(d0), torch.empty_like(df)
     out3 = torch.empty(3 * plan.n_prob, dtype=torch.float64, device=dev)
     gd = torch.empty_like(u)
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = getattr(wl, "e2e_steps", None) or max(3, args.steps // 2)
     lr = wl.step_kw["step"]
     barrier()
     torch.cuda.synchronize()
@@ -505,11 +543,12 @@ def run_ours(args, rank, world):
         print(json.dumps({
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "c64/f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "c128" if wl.prec == "f64" else "c64/f64", "data": "synthetic",
             "config": {"workload": wl.name, "precision": {"f32": "complex FP32 polynomial + sweeps; FP64 squaring, "
                                                                   "overlap, gradient accumulation",
                                                            "f32_all": "complex FP32 polynomial, squaring and sweeps; "
-                                                                      "FP64 overlap and gradient accumulation"}[wl.prec],
+                                                                      "FP64 overlap and gradient accumulation",
+                                                           "f64": "complex FP64 throughout"}[wl.prec],
                        "problems_per_step": wl.problems, "l2": "flushed between timed steps (256 MB write)",
                        "expm_kernels": [list(c) for c in plan.expm_classes()],
                        "parallelism": "replicas" if world > 1 else "single GPU"},
@@ -523,20 +562,29 @@ def run_ours(args, rank, world):
         }), flush=True)
 
 
-def main():
+def build_parser():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None, help="timed steps (default: the workload's)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d10")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d14")
+    ap.add_argument("--prec", choices=["default", "f64", "f32", "f32_all"], default="default",
+                    help="override the workload's precision")
     ap.add_argument("--autotune", action="store_true", help="tune the exponential kernels before timing")
     ap.add_argument("--expm-kernel", choices=["default", "tiled", "tc"], default="default",
                     help="force the exponential kernel: tiled CUDA-core or tcgen05 tensor-core")
     ap.add_argument("--ws-train", type=int, default=WS_TRAIN, help="warm-start training problems")
     ap.add_argument("--ws-held", type=int, default=WS_HELD, help="warm-start held-out problems")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = build_parser().parse_args()
+    if args.steps is None:
+        wl_cls = WORKLOADS.get(args.workload)
+        args.steps = wl_cls.default_steps if wl_cls is not None else 1
     args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

@@ -280,6 +280,17 @@ int qoc_plan_set_sweep_cluster(qoc_plan* plan, int cl);
 /* Current cluster size of the sweeps (0: one CTA per chain). */
 int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
 
+/* Slice derivatives of large blocks (Appendix B, Eq. propagator_differentiation, exact form):
+ * on = 1 (default for single-problem FP32 plans in exact mode) computes the derivative series of
+ * every unsplit slice of blocks with more than 128 states as tall GEMMs shared by all slices of a
+ * chunk: A_k x = -i tau (H0 x + sum_j u_kj Hc_j x) with H0, Hc_j the same for every slice, so one
+ * step of the power chains of all slices is [H0; Hc_1; ...] times a matrix of their vectors, and the
+ * Hc_j v products it yields are the ones the series contracts with.  on = 0 uses the per-slice series
+ * kernel.  The results agree to rounding.  The paper has no counterpart: it is a choice of kernels.
+ * qoc_plan_deriv_gemm: number of blocks on the GEMM path (0 if off or none qualifies). */
+int qoc_plan_set_deriv_gemm(qoc_plan* plan, int on);
+int qoc_plan_deriv_gemm(const qoc_plan* plan, int* blocks);
+
 /* Kernel choice of the batched exponentials (Sec. II.A, Eq. exppropagator, as in qoc_expm_blocks):
  * rule i applies to blocks of size m <= m_max[i] (rules are tried in increasing m_max; the first
  * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =
@@ -303,16 +314,20 @@ int qoc_plan_expm_classes(const qoc_plan* plan, int max_out, int* n_classes, int
                           int* m_max, int* n_blocks);
 
 /* ---------------------------------------------------------------- measurement */
-/* Phase timing: when enabled, every later call records CUDA events on its stream between its
- * phases.  qoc_plan_phase_times waits for the last call and writes up to n_out durations in ms:
- *   [0] assembly + batched expm, [1] forward/backward sweeps, [2] overlap, [3] slice derivatives,
- *   [4] gradient reduction / update.
+/* Phase timing: when enabled, every later call records CUDA events on its stream around each
+ * phase's launches.  qoc_plan_phase_times waits for the last call and writes up to n_out sums of its
+ * launch durations in ms, over every segment of a checkpointed call:
+ *   [0] assembly + batched exponentials (both passes when checkpointing), [1] forward/backward
+ *   sweeps, [2] overlap, [3] slice derivatives, [4] gradient reduction / update.
  * Work counters (reset by enabling): counts[0] = sum over (slice, block) items of m^3 times the
  * polynomial products taken (working precision), counts[1] = sum of m^3 times the squarings,
  * counts[2] = (slice, block) items exponentiated, counts[3] = complex multiply-adds of the exact
  * slice-derivative series done by the register-tile kernel (FP32 plans, unsplit slices): per item
  * (c (3P + 1) + n_ctrl) m^2 for c copies and series length P (2P matrix-vector products per copy,
- * the (P+1)-term M tile, the contraction with each Hc_j). */
+ * the (P+1)-term M tile, the contraction with each Hc_j); counts[4] = complex multiply-adds of the
+ * slice-derivative series of large blocks done as tall GEMMs (FP32 plans, m > 128, unsplit slices):
+ * per item (1 + n_ctrl) m^2 2c (P + 1) for the chains and c n_ctrl m (P + 1)(P + 2)/2 for the
+ * contraction. */
 int qoc_plan_set_profiling(qoc_plan* plan, int on);
 int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
 int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);

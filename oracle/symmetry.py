@@ -158,15 +158,18 @@ def dn_orbits(n: int):
     return orbits
 
 
-def dn_blocks(n: int):
+def dn_blocks(n: int, labels=None):
     """D_n-adapted basis.  Returns a list of (label, V) with V of shape [copies, m, 2^n]
-    (copies = irrep dimension); V[r, a] is the a-th basis vector of row r+1 of the irrep."""
+    (copies = irrep dimension); V[r, a] is the a-th basis vector of row r+1 of the irrep.
+    labels (optional): build only the irreps named there (same vectors as the full build)."""
     G = dn_group(n)
     orbits = dn_orbits(n)
     irreps = dn_irreps(n)
     dim = 1 << n
     out = []
     for label, d, D in irreps:
+        if labels is not None and label not in labels:
+            continue
         rows = [[] for _ in range(d)]
         for orb in orbits:
             idx = {x: i for i, x in enumerate(orb)}

@@ -317,9 +317,10 @@ class Plan:
 
     def work_counts(self) -> List[int]:
         """[sum m^3 * polynomial products, sum m^3 * squarings, items, complex multiply-adds of the
-        register-tile derivative series] since profiling was enabled."""
-        out = (C.c_longlong * 4)()
-        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 4), "qoc_plan_work_counts")
+        register-tile derivative series, complex multiply-adds of the GEMM-path derivative series]
+        since profiling was enabled."""
+        out = (C.c_longlong * 5)()
+        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 5), "qoc_plan_work_counts")
         return list(out)
 
     def set_expm_rules(self, rules) -> None:
@@ -342,6 +343,16 @@ class Plan:
         """Sweep kernel: cl = 2, 4 or 8 CTAs per chain in a thread-block cluster, 0 one CTA per
         chain, -1 the automatic choice."""
         L.check(self.lib.qoc_plan_set_sweep_cluster(self.handle, cl), "qoc_plan_set_sweep_cluster")
+
+    def set_deriv_gemm(self, on: bool) -> None:
+        """Large-block slice derivatives as tall GEMMs shared by a chunk's slices (True, the default
+        where it applies) or the per-slice series kernel (False)."""
+        L.check(self.lib.qoc_plan_set_deriv_gemm(self.handle, int(on)), "qoc_plan_set_deriv_gemm")
+
+    def deriv_gemm_blocks(self) -> int:
+        n = C.c_int()
+        L.check(self.lib.qoc_plan_deriv_gemm(self.handle, C.byref(n)), "qoc_plan_deriv_gemm")
+        return n.value
 
     def sweep_cluster(self) -> int:
         n = C.c_int()

@@ -75,7 +75,7 @@ template <class T>
 __global__ void __launch_bounds__(GRAD_THREADS)
 grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, const cx<T>* __restrict__ psi_st,
             const cx<T>* __restrict__ lam_st, double2* __restrict__ partial, char* __restrict__ scratch,
-            size_t slot_bytes, int a_in_smem, int max_m, int fast_m) {
+            size_t slot_bytes, int a_in_smem, int max_m, int fast_m, int gemm_min_m) {
     constexpr int PM = GradCfg<T>::P;
     constexpr int CG = GradCfg<T>::CG;
     extern __shared__ __align__(16) unsigned char dsm[];
@@ -112,7 +112,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
     __shared__ int s_nl;
     __shared__ int s_wc[32];
     // slices this launch owns: not those of the reverse-mode kernel (>= 2^REV_MIN_SUB sub-slices) nor
-    // the unsplit slices of register-sized blocks (grad_fast.cu)
+    // the unsplit slices of register-sized blocks (grad_fast.cu) or of GEMM-path blocks (grad_gemm.cu)
     auto want = [&](long long it) -> bool {
         int bi;
         long long k;
@@ -126,7 +126,7 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
         }
         const DevBlock& Bw = P.blocks[bi];
         const int sub = P.grad_mode == 0 ? slice_halvings(slice_beta(P, Bw, u, k), theta, MAX_SUB_LOG2) : 0;
-        return sub < REV_MIN_SUB && !(sub == 0 && Bw.m <= fast_m);
+        return sub < REV_MIN_SUB && !(sub == 0 && (Bw.m <= fast_m || (gemm_min_m > 0 && Bw.m >= gemm_min_m)));
     };
     for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
         const int nl = s_nl;
@@ -477,20 +477,21 @@ int grad_grid_limit(int prec, int max_m) {
 
 int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store,
                          double2* partial, char* scratch, size_t slot_bytes, int max_m, int grid,
-                         cudaStream_t st) {
+                         cudaStream_t st, int gemm_min_m) {
     if (P.nc > 8) return -2;
     if (P.prec == 0) {
         const size_t sm = grad_smem<double>(max_m);
         cudaFuncSetAttribute(grad_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<double><<<grid, GRAD_THREADS, sm, st>>>(P, 1e-17, 3.8, u, (const double2*)psi_store,
                                                            (const double2*)lam_store, partial, scratch, slot_bytes,
-                                                           grad_mode_of<double>(max_m), max_m, 0);
+                                                           grad_mode_of<double>(max_m), max_m, 0, 0);
     } else {
         const size_t sm = grad_smem<float>(max_m);
         cudaFuncSetAttribute(grad_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         grad_kernel<float><<<grid, GRAD_THREADS, sm, st>>>(P, GF32_SERIES_TOL, 3.0, u, (const float2*)psi_store,
                                                           (const float2*)lam_store, partial, scratch, slot_bytes,
-                                                          grad_mode_of<float>(max_m), max_m, grad_fast_max_m(P.prec));
+                                                          grad_mode_of<float>(max_m), max_m, grad_fast_max_m(P.prec),
+                                                          gemm_min_m);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }

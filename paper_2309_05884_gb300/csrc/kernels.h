@@ -54,6 +54,24 @@ int grad_fast_max_m(int prec);
 int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
                      int max_m, int grid, cudaStream_t st);
 
+// ---- grad_gemm.cu (exact slice derivatives of blocks with m >= grad_gemm_min_m(), FP32 plans, unsplit
+// slices: the series chains of every slice of a chunk as tall GEMMs with the stacked [H0; Hc_j])
+constexpr int GG_PCAP = 19;  // longest series (beta <= 3: beta^20 / 20! < 7.5e-9)
+struct GgBlock {
+    int bi;          // active block index
+    int m, c;        // size, active copies
+    int ncol;        // 2 c S columns of the chunk layout
+    long long x0, x1, y, z, w;  // complex offsets in the chunk scratch: X ping, X pong, Y, Z store, W store
+};
+int grad_gemm_min_m();
+// Offsets of every block for S slice slots per chunk, and the GEMM tile list (block, row tile, column
+// tile); returns the tile count, *elems the complex elements of the chunk scratch.
+int grad_gemm_layout(GgBlock* gb, int ngb, int nc, int S, int4* tiles, int max_tiles, size_t* elems);
+// aux: 32 + ngb * S ints of device scratch
+int launch_grad_gemm(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
+                     const GgBlock* gb, int ngb, const int4* tiles, int ntiles, int S, int* aux, void* scratch,
+                     cudaStream_t st);
+
 // ---- expm_tc.cu (tcgen05 tensor cores, FP16-split products; FP32 plans, m <= 112)
 int expm_tc_supported(int prec, int m);
 int expm_tc_grid_limit(int m_max);
@@ -92,9 +110,10 @@ int launch_store_final(const DevPlan& P, const void* fin, double2* psiN, long lo
 
 // ---- grad.cu
 // Per-slice, per-block partial derivatives do[k][b][j] = sum_r lam_k^dagger dU_k/du_kj psi_{k-1}.
+// gemm_min_m > 0: unsplit slices of blocks with m >= gemm_min_m belong to the GEMM path (grad_gemm.cu)
 int launch_grad_partials(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store,
                          double2* partial, char* scratch, size_t slot_bytes, int max_m, int grid,
-                         cudaStream_t st);
+                         cudaStream_t st, int gemm_min_m = 0);
 size_t grad_slot_bytes(int prec, int max_m);
 // Shared memory the slice-derivative kernel needs for its vector families (without A).
 size_t grad_vector_smem(int prec, int max_m);

@@ -89,6 +89,13 @@ struct qoc_plan {
     size_t grad_slot = 0;
     int rev_grid = 0;
     size_t rev_slot = 0;
+    // GEMM-path slice derivatives of large blocks (single-problem FP32 plans)
+    std::vector<GgBlock> gg;
+    int gg_S = 0, gg_ntiles = 0;
+    bool gg_on = true;
+    size_t gg_bytes = 0;
+    GgBlock* d_gg = nullptr;
+    int4* d_gg_tiles = nullptr;
     int seg = 0;                    // slices per checkpoint segment (single problem)
     int nseg = 1;                   // segments
     int64_t vlen = 0;               // complex elements of one boundary vector set (sum c*m)
@@ -112,12 +119,16 @@ struct qoc_plan {
     unsigned long long* d_stats = nullptr;
     bool profiling = false;
     bool capturing = false;
-    cudaEvent_t ev[6] = {};
+    // profiling: a pair of CUDA events around every phase launch of the last call (phase ids as in
+    // qoc_plan_phase_times), summed per phase on request
+    mutable std::vector<cudaEvent_t> sec_ev;
+    mutable std::vector<int> sec_phase;
     cudaGraphExec_t graph = nullptr;
     GraphKey graph_key{};
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
-           off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0, off_rev = 0;
+           off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0, off_rev = 0,
+           off_gg = 0, off_ggaux = 0;
     size_t el = 16;
     size_t ws_bytes = 0;
     int64_t u_elems = 0, s_elems = 0, part_rows = 0;
@@ -242,11 +253,44 @@ int check_norms(const qoc_plan* p, const double* a, const double* b, cudaStream_
     return QOC_OK;
 }
 
+// Start a call's phase log (profiling only).
+void sections_begin(const qoc_plan* p) {
+    if (p->profiling && !p->capturing) p->sec_phase.clear();
+}
+
+// Events on the launching stream around one phase's launches (profiling only, not while capturing).
+struct Timed {
+    const qoc_plan* p;
+    cudaStream_t st;
+    size_t idx = 0;
+    bool on;
+    Timed(const qoc_plan* p_, int phase, cudaStream_t s) : p(p_), st(s), on(p_->profiling && !p_->capturing) {
+        if (!on) return;
+        idx = 2 * p->sec_phase.size();
+        while (p->sec_ev.size() < idx + 2) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) {
+                (void)cudaGetLastError();
+                on = false;
+                return;
+            }
+            p->sec_ev.push_back(e);
+        }
+        p->sec_phase.push_back(phase);
+        cudaEventRecord(p->sec_ev[idx], st);
+    }
+    ~Timed() {
+        if (on) cudaEventRecord(p->sec_ev[idx + 1], st);
+    }
+};
+enum { PH_EXPM = 0, PH_SWEEPS = 1, PH_OVERLAP = 2, PH_DERIV = 3, PH_REDUCE = 4 };
+
 char* ckpt_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_ckpt + (size_t)i * p->vlen * p->el; }
 char* lamb_vec(const qoc_plan* p, char* ws, int i) { return ws + p->off_lamb + (size_t)i * p->vlen * p->el; }
 
 // nk < 0: whole-problem launches over every block; nk >= 0: slice window [k0, k0 + nk) of one problem
 int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
+    Timed tm(p, PH_EXPM, st);
     const DevPlan P = p->dev(k0, nk);
     for (const auto& c : p->classes) {
         int rc;
@@ -276,6 +320,7 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
 
 int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char* fwd_in, char* fwd_out,
                const char* bwd_in, char* bwd_out, cudaStream_t st) {
+    Timed tm(p, PH_SWEEPS, st);
     const DevPlan P = p->dev(k0, nk);
     const int rc = p->sweep_cl > 0
                        ? launch_sweeps_cluster(P, ws + p->off_U, fwd_in, fwd_out, bwd_in, bwd_out, ws + p->off_psi,
@@ -288,12 +333,20 @@ int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char
 }
 
 int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
+    Timed tm(p, PH_DERIV, st);
     const DevPlan P = p->dev(k0, nk);
+    const bool gon = p->gg_on && !p->gg.empty();
+    const int gmin = gon ? grad_gemm_min_m() : 0;
     const int g = launch_grad_partials(P, u, ws + p->off_psi, ws + p->off_lam,
                                        reinterpret_cast<double2*>(ws + p->off_partial), ws + p->off_grad,
-                                       p->grad_slot, p->max_m, p->grad_grid, st);
+                                       p->grad_slot, p->max_m, p->grad_grid, st, gmin);
     if (g == -2) return set_error(QOC_EUNSUPPORTED, "gradient kernel limits exceeded");
     if (g != 0) return cuda_fail(cudaGetLastError(), "gradient launch");
+    if (gon &&
+        launch_grad_gemm(P, u, ws + p->off_psi, ws + p->off_lam, reinterpret_cast<double2*>(ws + p->off_partial),
+                         p->d_gg, (int)p->gg.size(), p->d_gg_tiles, p->gg_ntiles, p->gg_S,
+                         reinterpret_cast<int*>(ws + p->off_ggaux), ws + p->off_gg, st) != 0)
+        return cuda_fail(cudaGetLastError(), "gradient launch (GEMM path)");
     if (launch_grad_fast(P, u, ws + p->off_psi, ws + p->off_lam, reinterpret_cast<double2*>(ws + p->off_partial),
                          p->max_m, p->gf_grid, st) != 0)
         return cuda_fail(cudaGetLastError(), "gradient launch (register tiles)");
@@ -447,6 +500,8 @@ void layout_workspace(qoc_plan* p, int64_t u_elems, int64_t s_elems, int64_t par
     p->off_expm = off;    off = align_up(off + p->expm_scratch, 256);
     p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
     p->off_rev = off;     off = align_up(off + p->rev_slot * (size_t)p->rev_grid, 256);
+    p->off_gg = off;      off = align_up(off + p->gg_bytes, 256);
+    p->off_ggaux = off;   off = align_up(off + sizeof(int) * (32 + p->gg.size() * (size_t)p->gg_S), 256);
     p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
     p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
     p->off_adam = off;    off = align_up(off + (size_t)2 * p->rows * p->nc * sizeof(double), 256);
@@ -462,40 +517,36 @@ UpdateRule no_update() {
     return r;
 }
 
-// Phase events: [0]..[1] propagators (and forward sweeps when checkpointing), [1]..[2] sweeps,
-// [2]..[3] overlap, [3]..[4] slice derivatives (with checkpointing: the whole costate pass),
-// [4]..[5] reduction / update.
+// One F (+ gradient, + update) evaluation.  Without checkpointing the forward states and costates
+// run in one sweep launch; with it, the costate pass recomputes each segment's propagators.
 int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3,
                        double* grad, double* u_update, const UpdateRule& rule, char* w, cudaStream_t st) {
     int rc;
     const DevPlan P = p->dev();
-    auto mark = [&](int i) {
-        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
-    };
+    sections_begin(p);
     const bool want_grad = grad || u_update;
     double2* o_ws = reinterpret_cast<double2*>(w + p->off_o);
-    mark(0);
     if (p->nseg == 1) {
         if (launch_gather(P, reinterpret_cast<const double2*>(psi0), ckpt_vec(p, w, 0), st) != 0 ||
             (want_grad && launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0))
             return cuda_fail(cudaGetLastError(), "gather launch");
         if ((rc = run_expm(p, u, w, 0, -1, st))) return rc;
-        mark(1);
         if ((rc = run_sweeps(p, w, 0, -1, want_grad ? 3 : 1, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1), lamb_vec(p, w, 0),
                              lamb_vec(p, w, 1), st)))
             return rc;
-        mark(2);
-        if (launch_overlap(P, ckpt_vec(p, w, 1), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
-            return cuda_fail(cudaGetLastError(), "overlap launch");
-        mark(3);
+        {
+            Timed tm(p, PH_OVERLAP, st);
+            if (launch_overlap(P, ckpt_vec(p, w, 1), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+                return cuda_fail(cudaGetLastError(), "overlap launch");
+        }
         if (want_grad && (rc = run_grad(p, u, w, 0, -1, st))) return rc;
     } else {
         if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
-        mark(1);
-        mark(2);
-        if (launch_overlap(P, ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
-            return cuda_fail(cudaGetLastError(), "overlap launch");
-        mark(3);
+        {
+            Timed tm(p, PH_OVERLAP, st);
+            if (launch_overlap(P, ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3, o_ws, st) != 0)
+                return cuda_fail(cudaGetLastError(), "overlap launch");
+        }
         if (want_grad) {
             if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
                 return cuda_fail(cudaGetLastError(), "gather launch");
@@ -513,13 +564,12 @@ int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, c
             }
         }
     }
-    mark(4);
     if (want_grad) {
+        Timed tm(p, PH_REDUCE, st);
         if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial), o_ws, grad, u_update, rule,
                                out3, st) != 0)
             return cuda_fail(cudaGetLastError(), "reduce launch");
     }
-    mark(5);
     return QOC_OK;
 }
 
@@ -528,17 +578,12 @@ int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, c
 int forward_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3, char* w,
                  cudaStream_t st) {
     int rc;
-    auto mark = [&](int i) {
-        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
-    };
-    mark(0);
+    sections_begin(p);
     if ((rc = forward_pass(p, u, psi0, w, st))) return rc;
-    mark(1);
-    mark(2);
+    Timed tm(p, PH_OVERLAP, st);
     if (launch_overlap(p->dev(), ckpt_vec(p, w, p->nseg), reinterpret_cast<const double2*>(psif), out3,
                        reinterpret_cast<double2*>(w + p->off_o), st) != 0)
         return cuda_fail(cudaGetLastError(), "overlap launch");
-    mark(3);
     return QOC_OK;
 }
 
@@ -547,9 +592,7 @@ int forward_impl(const qoc_plan* p, const double* u, const double* psi0, const d
 int backward_impl(const qoc_plan* p, const double* u, const double* psif, const double* gF, double* grad, char* w,
                   cudaStream_t st) {
     int rc;
-    auto mark = [&](int i) {
-        if (p->profiling && !p->capturing) cudaEventRecord(p->ev[i], st);
-    };
+    sections_begin(p);
     const DevPlan P = p->dev();
     if (launch_gather(P, reinterpret_cast<const double2*>(psif), lamb_vec(p, w, 0), st) != 0)
         return cuda_fail(cudaGetLastError(), "gather launch");
@@ -569,14 +612,13 @@ int backward_impl(const qoc_plan* p, const double* u, const double* psif, const 
             cur ^= 1;
         }
     }
-    mark(4);
     UpdateRule rule = no_update();
     rule.gscale = gF;
+    Timed tm(p, PH_REDUCE, st);
     if (launch_grad_reduce(P, reinterpret_cast<const double2*>(w + p->off_partial),
                            reinterpret_cast<const double2*>(w + p->off_o), grad, nullptr, rule,
                            reinterpret_cast<const double*>(w + p->off_out3), st) != 0)
         return cuda_fail(cudaGetLastError(), "reduce launch");
-    mark(5);
     return QOC_OK;
 }
 
@@ -787,6 +829,25 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         p->rev_grid = (int)std::max<long long>(1, std::min<long long>({grad_items, (long long)sms, by_mem}));
     }
 
+    // large blocks' slice derivatives as tall GEMMs (single-problem FP32 plans, exact mode)
+    if (o.prec != QOC_PREC_F64 && o.grad_mode == 0 && n_problems == 1) {
+        for (int bi = 0; bi < p->nb; ++bi)
+            if (p->hblocks[bi].m >= grad_gemm_min_m()) {
+                GgBlock G{};
+                G.bi = bi;
+                G.m = p->hblocks[bi].m;
+                G.c = p->hblocks[bi].c;
+                p->gg.push_back(G);
+            }
+        if (!p->gg.empty()) {
+            const int slots = p->nseg == 1 ? Ns[0] : p->seg;
+            p->gg_S = std::min(64, slots);
+            size_t elems = 0;
+            p->gg_ntiles = grad_gemm_layout(p->gg.data(), (int)p->gg.size(), nc, p->gg_S, nullptr, 0, &elems);
+            p->gg_bytes = elems * sizeof(float2);
+        }
+    }
+
     // workspace layout
     p->u_elems = u_off;
     p->s_elems = s_off;
@@ -815,6 +876,13 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     QOC_UP(p->d_prob_blocks, p->prob_blocks.data(), p->prob_blocks.size(), "upload problems");
     QOC_UP(p->d_prob_block_off, p->prob_block_off.data(), p->prob_block_off.size(), "upload problems");
     QOC_UP(p->d_H64, reinterpret_cast<double2*>(H64.data()), H64.size(), "upload H");
+    if (!p->gg.empty()) {
+        std::vector<int4> tl(p->gg_ntiles);
+        size_t elems = 0;
+        grad_gemm_layout(p->gg.data(), (int)p->gg.size(), nc, p->gg_S, tl.data(), p->gg_ntiles, &elems);
+        QOC_UP(p->d_gg, p->gg.data(), p->gg.size(), "upload GEMM-path blocks");
+        QOC_UP(p->d_gg_tiles, tl.data(), tl.size(), "upload GEMM-path tiles");
+    }
     {
         std::vector<int64_t> ps;
         for (const auto& pr : p->probs) {
@@ -829,12 +897,10 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     *p->h_status = 0;
     if ((e = cudaEventCreateWithFlags(&p->st_ev, cudaEventDisableTiming)) != cudaSuccess)
         return fail(e, "cudaEventCreate");
-    if ((e = cudaMalloc(&p->d_stats, 4 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc stats");
-    cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
+    if ((e = cudaMalloc(&p->d_stats, 8 * sizeof(unsigned long long))) != cudaSuccess) return fail(e, "cudaMalloc stats");
+    cudaMemset(p->d_stats, 0, 8 * sizeof(unsigned long long));
     cudaMemset(p->d_status, 0, sizeof(int));
 #undef QOC_UP
-    for (auto& ev : p->ev)
-        if ((e = cudaEventCreate(&ev)) != cudaSuccess) return fail(e, "cudaEventCreate");
     if (o.prec == QOC_PREC_F64) {
         p->d_H = p->d_H64;
     } else {
@@ -871,12 +937,14 @@ void qoc_plan_free(qoc_plan* p) {
     cudaFree(p->d_items);
     cudaFree(p->d_prob_blocks);
     cudaFree(p->d_prob_block_off);
+    cudaFree(p->d_gg);
+    cudaFree(p->d_gg_tiles);
     cudaFree(p->d_status);
     cudaFree(p->d_prob_state);
     if (p->h_status) cudaFreeHost(p->h_status);
     if (p->st_ev) cudaEventDestroy(p->st_ev);
     cudaFree(p->d_stats);
-    for (auto& ev : p->ev)
+    for (auto& ev : p->sec_ev)
         if (ev) cudaEventDestroy(ev);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     delete p;
@@ -925,32 +993,36 @@ int qoc_plan_set_profiling(qoc_plan* p, int on) {
     if (!p) return set_error(QOC_EINVAL, "null plan");
     cudaSetDevice(p->device);
     p->profiling = on != 0;
-    if (on) cudaMemset(p->d_stats, 0, 4 * sizeof(unsigned long long));
+    if (on) cudaMemset(p->d_stats, 0, 8 * sizeof(unsigned long long));
     return QOC_OK;
 }
 
 int qoc_plan_phase_times(qoc_plan* p, float* ms, int n) {
     if (!p || !ms) return set_error(QOC_EINVAL, "null argument");
     if (!p->profiling) return set_error(QOC_EINVAL, "profiling is off");
+    if (p->sec_phase.empty()) return set_error(QOC_EINVAL, "no call was timed since profiling was enabled");
     cudaSetDevice(p->device);
-    cudaError_t e = cudaEventSynchronize(p->ev[5]);
+    const size_t last = 2 * p->sec_phase.size() - 1;
+    cudaError_t e = cudaEventSynchronize(p->sec_ev[last]);
     if (e != cudaSuccess) return cuda_fail(e, "event synchronize");
-    for (int i = 0; i < n && i < 5; ++i) {
+    float acc[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    for (size_t i = 0; i < p->sec_phase.size(); ++i) {
         float t = 0.f;
-        e = cudaEventElapsedTime(&t, p->ev[i], p->ev[i + 1]);
+        e = cudaEventElapsedTime(&t, p->sec_ev[2 * i], p->sec_ev[2 * i + 1]);
         if (e != cudaSuccess) return cuda_fail(e, "event elapsed");
-        ms[i] = t;
+        acc[p->sec_phase[i]] += t;
     }
+    for (int i = 0; i < n && i < 5; ++i) ms[i] = acc[i];
     return QOC_OK;
 }
 
 int qoc_plan_work_counts(qoc_plan* p, long long* out, int n) {
     if (!p || !out) return set_error(QOC_EINVAL, "null argument");
     cudaSetDevice(p->device);
-    unsigned long long h[4] = {0, 0, 0, 0};
+    unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaError_t e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats read");
-    for (int i = 0; i < n && i < 4; ++i) out[i] = (long long)h[i];
+    for (int i = 0; i < n && i < 5; ++i) out[i] = (long long)h[i];
     return QOC_OK;
 }
 
@@ -968,8 +1040,13 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
             ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
         }
     }
-    // register-tile derivative launch per gradient pass (FP32 plans)
-    const int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
+    // register-tile derivative launch per gradient pass (FP32 plans), plus the GEMM path's chunks:
+    // prep, load, (GG_PCAP + 1) GEMM + combine steps, contraction
+    int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
+    if (p->gg_on && !p->gg.empty() && p->opts.grad_mode == 0) {
+        const int slots = p->nseg == 1 ? p->N : p->seg;
+        gfl += ((slots + p->gg_S - 1) / p->gg_S) * (3 + 2 * (GG_PCAP + 1));
+    }
     if (p->nseg == 1)
         *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + nrev + 1 : 1 + ncls + 1 + 1;
     else
@@ -988,6 +1065,24 @@ int qoc_plan_set_sweep_cluster(qoc_plan* p, int cl) {
     if (cl > 0 && !sweep_cluster_fits(p->opts.prec, p->max_m, p->max_c, cl))
         return set_error(QOC_EUNSUPPORTED, "cluster sweep buffers do not fit in shared memory");
     p->sweep_cl = cl;
+    return QOC_OK;
+}
+
+int qoc_plan_set_deriv_gemm(qoc_plan* p, int on) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    if (on != 0 && on != 1) return set_error(QOC_EINVAL, "on must be 0 or 1");
+    p->gg_on = on != 0;
+    if (p->graph) {
+        cudaSetDevice(p->device);
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    return QOC_OK;
+}
+
+int qoc_plan_deriv_gemm(const qoc_plan* p, int* blocks) {
+    if (!p || !blocks) return set_error(QOC_EINVAL, "null argument");
+    *blocks = p->gg_on ? (int)p->gg.size() : 0;
     return QOC_OK;
 }
 

@@ -9,8 +9,11 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
+    # the D_10 workload keeps this CPU test short; the default (D_14) arm runs the same code on a
+    # 2-slice sample per step
     out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                          "--warmup", "0"], cwd=ROOT, capture_output=True, text=True, timeout=600)
+                          "--warmup", "0", "--workload", "d10"], cwd=ROOT, capture_output=True, text=True,
+                         timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
     lines = [ln for ln in out.stdout.splitlines() if ln.startswith("{")]
     assert len(lines) == 1
@@ -24,3 +27,10 @@ def test_reference_arm_json_line():
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("D_10 XXZ ring")
+
+
+def test_default_workload_is_d14():
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.build_parser().parse_args([]).workload == "d14"
+    assert bench.WORKLOADS["d14"].default_steps >= 1
