@@ -244,10 +244,12 @@ class SnBatch:
     """256 independent S_n problems per launch (batched many-problem solve)."""
     name = SN_WORKLOAD
     problems = SN_BATCH
-    prec = "f32_all"
+    # FP64: at T = 10 slice norms reach |tau H| ~ 200, where an FP32 polynomial leaves ~1e-3 in the
+    # final states (the parity bound is met in FP64 only)
+    prec = "f64"
     step_kw = dict(step=0.02, rule="fixed")
     key = "sn-batch"
-    default_steps = 20
+    default_steps = 3
 
     def build(self, api, dev):
         probs = sn_batch_problems()

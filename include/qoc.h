@@ -150,8 +150,22 @@ typedef struct qoc_plan_opts {
                              slices of propagators; the costate pass recomputes each segment's
                              propagators and states (twice the exponentials, workspace ~ N/S + S
                              states and S propagators per block); -1 = S = ceil(sqrt(N)) */
-    int reserved[4];
+    int objective;        /* QOC_OBJ_STATE (default) or QOC_OBJ_GATE, see below */
+    int reserved[3];
 } qoc_plan_opts;
+
+/* Objectives.
+ *   QOC_OBJ_STATE: state transfer, F = |<psi_f|psi_N>|^2 (Sec. II.A, Eq. probability); block states
+ *     as described under Conventions, the copies selected by the active mask.
+ *   QOC_OBJ_GATE: gate (unitary) fidelity, the trace fidelity of Sec. IV with a target gate W:
+ *     F = |Tr(W^dagger U_N ... U_1) / d|^2, d = 2^n.  For a symmetric W (one that commutes with the
+ *     group, as the gates of Sec. III do) both are block diagonal and every copy of block b carries
+ *     the same W_b, so Tr(W^dagger U) = sum_b c_b Tr(W_b^dagger U_b).  The plan propagates every column
+ *     of every block: block states have the layout [block b][column r][m_b] (length sum_b m_b^2), the
+ *     caller passes psi0 = sqrt(c_b / d) times the identity columns and psif = sqrt(c_b / d) times the
+ *     columns of W_b, so that sum_b sum_r <psif_br|psi_N,br> = Tr(W^dagger U) / d and out3, the
+ *     gradient and the optimiser work unchanged.  No active mask (every column takes part). */
+enum { QOC_OBJ_STATE = 0, QOC_OBJ_GATE = 1 };
 
 void qoc_plan_opts_default(qoc_plan_opts* opts);
 
@@ -360,6 +374,30 @@ int qoc_adam_step(float* param, uint16_t* shadow_bf16, const float* grad, float*
                   float beta1, float beta2, float eps, int t, void* stream);
 int qoc_mse(const float* Y, const float* T, float* dY, double* loss, long long n, void* stream);
 int qoc_to_bf16(const float* x, uint16_t* y, long long n, void* stream);
+
+/* ---------------------------------------------------------------- Trotterised per-qubit controls */
+/* Sec. IV (Eqs. Hcprime, completeH_cpl, propagator_cpl, propagator_cpl_transformed): with one pulse
+ * pair per qubit the Hamiltonian H_j = sum_i h_i^(j) + H_cpl has no symmetry left, and the slice
+ * propagator is approximated by the ordered product (factor i = 1 leftmost)
+ *     U_j = prod_{i=1..n} exp(-i tau h_i^(j)) E,   E = exp(-i tau/n H_cpl),
+ *     h_i^(j) = 1/2 (Bz_ij sigma_z^(i) + Bx_ij sigma_x^(i) + By_ij sigma_y^(i)),
+ * i.e. one 2 x 2 exponential per qubit and slice and a constant coupling factor that, H_cpl being
+ * D_n symmetric, is E = A_D (direct sum over blocks of exp(-i tau/n H_cpl,b)) A_D^dagger: one block
+ * exponential each, computed once by qoc_trotter_create.  States live in the full 2^n space.
+ *
+ * qoc_trotter_create: cpl is a D_n basis (every block, with vectors) whose H0 is H_cpl (its controls
+ *   are not used); tau the slice length.  n <= 12 (QOC_EUNSUPPORTED beyond: the kernel keeps two
+ *   2^n-amplitude buffers per CTA in shared memory).  Allocates device tables; free with
+ *   qoc_trotter_free.  Errors: QOC_EINVAL (not D_n, missing blocks or vectors, bad tau), QOC_ECUDA.
+ * qoc_trotter_propagate: psi_out[c] = U_N ... U_1 psi_in[c] for ncols full-space states (dev,
+ *   [ncols][2^n] complex128, psi_out must not alias psi_in); pulses dev [N][n][3] doubles
+ *   (Bz, Bx, By of qubit i in slice j at ((j * n) + i) * 3).  Columns = the identity gives the
+ *   propagator K.  FP64.  Asynchronous on stream. */
+typedef struct qoc_trotter qoc_trotter;
+int qoc_trotter_create(const qoc_basis* cpl, double tau, qoc_trotter** out);
+int qoc_trotter_propagate(const qoc_trotter* tr, const double* pulses, int N, const double* psi_in, double* psi_out,
+                          long long ncols, void* stream);
+void qoc_trotter_free(qoc_trotter* tr);
 
 /* ---------------------------------------------------------------- allocation-free variant */
 /* The paper has no counterpart to this entry point; it serves callers that cannot allocate device

@@ -26,6 +26,8 @@ QOC_RULE_FIXED = 0
 QOC_RULE_ADAM = 1
 QOC_BASIS_FIRST_BLOCK_ONLY = 1
 QOC_BASIS_NO_VECTORS = 2
+QOC_OBJ_STATE = 0
+QOC_OBJ_GATE = 1
 
 
 class qoc_term(C.Structure):
@@ -40,7 +42,7 @@ class qoc_system_desc(C.Structure):
 
 class qoc_plan_opts(C.Structure):
     _fields_ = [("prec", C.c_int), ("grad_mode", C.c_int), ("max_squarings", C.c_int),
-                ("ckpt_segment", C.c_int), ("reserved", C.c_int * 4)]
+                ("ckpt_segment", C.c_int), ("objective", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class qoc_opt_opts(C.Structure):
@@ -99,6 +101,9 @@ SIGNATURES = {
     "qoc_mse": (C.c_int, [P, P, P, P, C.c_longlong, P]),
     "qoc_to_bf16": (C.c_int, [P, P, C.c_longlong, P]),
     "qoc_tc_cgemm": (C.c_int, [P, P, P, C.c_int, C.c_longlong, P, P]),
+    "qoc_trotter_create": (C.c_int, [P, C.c_double, C.POINTER(P)]),
+    "qoc_trotter_propagate": (C.c_int, [P, P, C.c_int, P, P, C.c_longlong, P]),
+    "qoc_trotter_free": (None, [P]),
     "qoc_strerror": (C.c_char_p, [C.c_int]),
     "qoc_last_error": (C.c_char_p, []),
     "qoc_version": (C.c_int, []),

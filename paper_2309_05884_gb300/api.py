@@ -99,6 +99,25 @@ class Basis:
                 out.append(np.linalg.norm(blk[off + r * m: off + (r + 1) * m]))
         return np.array(out)
 
+    def gate_blocks(self, W: np.ndarray, tol: float = 1e-10) -> List[np.ndarray]:
+        """W_b = V_b^dagger W V_b (copy 0) of a full-space gate W that commutes with the symmetry group;
+        raises if W mixes blocks (it is then not a symmetric gate)."""
+        W = np.asarray(W, dtype=np.complex128)
+        assert W.shape == (self.full_dim, self.full_dim)
+        out = []
+        for b, (_, m, c, off) in enumerate(self.blocks):
+            Wb = np.zeros((m, m), np.complex128)
+            for a in range(m):
+                e = np.zeros(self.state_len, np.complex128)
+                e[off + a] = 1.0
+                col = self.state_to_blocks(W @ self.blocks_to_state(e))
+                Wb[:, a] = col[off: off + m]
+                col[off: off + m] = 0
+                if np.abs(col).max(initial=0.0) > tol:
+                    raise ValueError("the gate mixes symmetry blocks (it does not commute with the group)")
+            out.append(Wb)
+        return out
+
     def active_copies(self, psi0_blk: np.ndarray, psif_blk: np.ndarray, tol: float = 1e-13) -> np.ndarray:
         """Copies with support in both states (only those can contribute to <psi_f|psi_N>)."""
         return ((self.copy_norms(psi0_blk) > tol) & (self.copy_norms(psif_blk) > tol)).astype(np.uint8)
@@ -111,7 +130,7 @@ class Plan:
     PRECS = {"f64": L.QOC_PREC_F64, "f32": L.QOC_PREC_F32, "f32_all": L.QOC_PREC_F32_ALL}
 
     def __init__(self, basis, N, dt, prec: str = "f64", grad_mode: int = 0, active=None,
-                 max_squarings: int = 16, ckpt_segment: int = 0, device=None):
+                 max_squarings: int = 16, ckpt_segment: int = 0, device=None, objective: str = "state"):
         self.lib = L.load()
         batch = not isinstance(basis, Basis)
         self.bases = list(basis) if batch else [basis]
@@ -129,6 +148,8 @@ class Plan:
         opts.grad_mode = grad_mode
         opts.max_squarings = max_squarings
         opts.ckpt_segment = ckpt_segment
+        opts.objective = {"state": L.QOC_OBJ_STATE, "gate": L.QOC_OBJ_GATE}[objective]
+        self.objective = objective
         self.prec = prec
         self._acts = [None if a_ is None else np.ascontiguousarray(a_, dtype=np.uint8) for a_ in acts]
         for a_, b_ in zip(self._acts, self.bases):
@@ -254,6 +275,19 @@ class Plan:
         L.check(self.lib.qoc_expm_blocks(self.handle, _ptr(u), _ptr(out), _ptr(ws), ws.numel(), _stream(stream)),
                 "qoc_expm_blocks")
         return out
+
+    def gate_states(self, W_blocks) -> Tuple[np.ndarray, np.ndarray]:
+        """(psi0, psif) block states of a gate plan (one problem): in block b the identity columns and
+        the columns of W_b, both weighted by sqrt(c_b / d), d = sum_b c_b m_b."""
+        assert self.objective == "gate"
+        B = self.basis
+        d = sum(c * m for _, m, c, _ in B.blocks)
+        psi0, psif = [], []
+        for (_, m, c, _), Wb in zip(B.blocks, W_blocks):
+            w = np.sqrt(c / d)
+            psi0.append((w * np.eye(m, dtype=np.complex128)).T.reshape(-1))   # column r at [r*m, (r+1)*m)
+            psif.append((w * np.asarray(Wb, dtype=np.complex128)).T.reshape(-1))
+        return np.concatenate(psi0), np.concatenate(psif)
 
     def active_blocks(self) -> List[int]:
         """Basis indices of blocks with at least one active copy (the export layout's order)."""
@@ -399,6 +433,38 @@ class FidelityGrad(torch.autograd.Function):
             gFd = gFd.expand(plan.n_prob).contiguous()
         g = plan.backward(ctx.u, ctx.psif, ctx.serial, gF=gFd)
         return g, None, None, None
+
+
+class Trotter:
+    """Trotterised propagation with one pulse pair per qubit (Sec. IV): slice j applies
+    prod_{i=1..n} exp(-i tau h_i^(j)) E with E = exp(-i tau/n H_cpl) from the D_n blocks of the coupling
+    (qoc_trotter_create / qoc_trotter_propagate).  cpl: a D_n Basis whose H0 is H_cpl."""
+
+    def __init__(self, cpl: Basis, tau: float, device=None):
+        self.lib = L.load()
+        self.n, self.dim, self.tau = cpl.system.n, 1 << cpl.system.n, tau
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        h = C.c_void_p()
+        with torch.cuda.device(self.device):
+            L.check(self.lib.qoc_trotter_create(cpl.handle, float(tau), C.byref(h)), "qoc_trotter_create")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            self.lib.qoc_trotter_free(self.handle)
+            self.handle = None
+
+    def propagate(self, pulses: torch.Tensor, psi_in: torch.Tensor, stream=None) -> torch.Tensor:
+        """pulses [N, n, 3] (Bz, Bx, By) float64; psi_in [ncols, 2^n] complex128 -> U_N ... U_1 psi_in."""
+        assert pulses.dtype == torch.float64 and pulses.is_cuda and pulses.is_contiguous()
+        assert pulses.dim() == 3 and pulses.shape[1] == self.n and pulses.shape[2] == 3
+        assert psi_in.dtype == torch.complex128 and psi_in.is_cuda and psi_in.is_contiguous()
+        assert psi_in.shape[-1] == self.dim
+        out = torch.empty_like(psi_in)
+        ncols = psi_in.numel() // self.dim
+        L.check(self.lib.qoc_trotter_propagate(self.handle, _ptr(pulses), pulses.shape[0], _ptr(psi_in), _ptr(out),
+                                               ncols, _stream(stream)), "qoc_trotter_propagate")
+        return out
 
 
 def to_device(blk: np.ndarray, device=None) -> torch.Tensor:

@@ -46,6 +46,7 @@ struct Problem {
     int N;
     double dt;
     int64_t state_off;  // complex offset of this problem's block state in the concatenated states
+    int64_t state_len;  // its length (the basis' state length, or sum_b m_b^2 for the gate objective)
     int64_t u_row;      // first pulse row
 };
 
@@ -649,6 +650,11 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     if (o.max_squarings > 40) return set_error(QOC_EINVAL, "max_squarings must be <= 40");
     if (o.ckpt_segment < -1) return set_error(QOC_EINVAL, "ckpt_segment must be -1, 0 or positive");
     if (o.ckpt_segment != 0 && n_problems > 1) return set_error(QOC_EINVAL, "checkpointing needs a single-problem plan");
+    if (o.objective != QOC_OBJ_STATE && o.objective != QOC_OBJ_GATE) return set_error(QOC_EINVAL, "unknown objective");
+    const bool gate = o.objective == QOC_OBJ_GATE;
+    if (gate && actives)
+        for (int i = 0; i < n_problems; ++i)
+            if (actives[i]) return set_error(QOC_EINVAL, "the gate objective uses every column of every block: pass no active mask");
     const int nc = bases[0] ? bases[0]->n_ctrl : 0;
     for (int i = 0; i < n_problems; ++i) {
         if (!bases[i]) return set_error(QOC_EINVAL, "null basis");
@@ -672,8 +678,13 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     int64_t state_off = 0, u_row = 0;
     int maxN = 0;
     for (int i = 0; i < n_problems; ++i) {
-        p->probs.push_back({bases[i], Ns[i], dts[i], state_off, u_row});
-        state_off += bases[i]->state_len;
+        int64_t len = bases[i]->state_len;
+        if (gate) {
+            len = 0;
+            for (const auto& blk : bases[i]->blocks) len += (int64_t)blk.m * blk.m;
+        }
+        p->probs.push_back({bases[i], Ns[i], dts[i], state_off, len, u_row});
+        state_off += len;
         u_row += Ns[i];
         maxN = std::max(maxN, Ns[i]);
     }
@@ -696,6 +707,11 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         for (int b = 0; b < (int)B->blocks.size(); ++b) {
             const auto& blk = B->blocks[b];
             Act a{i, b, {}};
+            if (gate) {  // the m columns of the block's unitary
+                for (int r = 0; r < blk.m; ++r) a.copies.push_back(r);
+                acts.push_back(std::move(a));
+                continue;
+            }
             for (int r = 0; r < blk.c; ++r, ++copy_counter)
                 if (!actives || !actives[i] || actives[i][copy_counter]) a.copies.push_back(r);
             if (!a.copies.empty()) acts.push_back(std::move(a));
@@ -735,7 +751,12 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         d.h0_norm1 = blk.h0_norm1;
         for (int j = 0; j < nc; ++j) d.hc_norm1[j] = blk.hc_norm1[j];
         p->copy_base.push_back((int64_t)p->copy_src.size());
-        for (int r : a.copies) p->copy_src.push_back(pr.state_off + blk.offset + (int64_t)r * blk.m);
+        int64_t boff = blk.offset;
+        if (gate) {  // block-state layout of the gate objective: [block][column][m]
+            boff = 0;
+            for (int b2 = 0; b2 < a.b; ++b2) boff += (int64_t)pr.basis->blocks[b2].m * pr.basis->blocks[b2].m;
+        }
+        for (int r : a.copies) p->copy_src.push_back(pr.state_off + boff + (int64_t)r * blk.m);
         H64.insert(H64.end(), blk.h0.begin(), blk.h0.end());
         H64.insert(H64.end(), blk.hc.begin(), blk.hc.end());
         h_off += (int64_t)(1 + nc) * blk.m * blk.m;
@@ -887,7 +908,7 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         std::vector<int64_t> ps;
         for (const auto& pr : p->probs) {
             ps.push_back(pr.state_off);
-            ps.push_back(pr.basis->state_len);
+            ps.push_back(pr.state_len);
         }
         QOC_UP(p->d_prob_state, ps.data(), ps.size(), "upload problems");
     }
