@@ -90,8 +90,8 @@ SN_WORKLOAD = (f"{SN_BATCH} independent S_n problems (H0 = J sum_{{i<j}} Z_i Z_j
                f"D(n,k), k ~ U{{0..n}}, pulses U[-1,1], seeds 10000+i; block J = n/2 (size n+1) per problem")
 
 
-def sn_batch_problems():
-    return I.sn_problem_batch(SN_BATCH, base_seed=10_000)
+def sn_batch_problems(count: int = SN_BATCH):
+    return I.sn_problem_batch(count, base_seed=10_000)
 
 
 # --------------------------------------------------------------------------- clocks
@@ -252,7 +252,7 @@ class SnBatch:
     default_steps = 3
 
     def build(self, api, dev):
-        probs = sn_batch_problems()
+        probs = sn_batch_problems(self.problems)
         self._probs = probs
         systems = [I.sn_allpairs(p.n, p.J, p.h, SN_T, p.N) for p in probs]
         bases = [api.Basis(s, first_block_only=True, vectors=False) for s in systems]
@@ -398,7 +398,19 @@ def run_ours(args, rank, world):
     wl = WORKLOADS[args.workload]()
     if args.prec != "default":
         wl.prec = args.prec
+    if args.sn_problems and args.workload == "sn-batch":
+        wl.problems = args.sn_problems
     plan, u0, b0, bf = wl.build(api, dev)
+    if args.ncu:
+        # profiling mode: one GRAPE step and nothing else (no warm-up, timing, copies or CPU leg), so
+        # that a launch list or a capture covers exactly one step; its output is not a bench line
+        u = torch.from_numpy(u0.copy()).to(dev)
+        plan.optimize(u, api.to_device(b0, dev), api.to_device(bf, dev), iters=1, **wl.step_kw)
+        torch.cuda.synchronize()
+        plan.sync_status()
+        if rank == 0:
+            print(json.dumps({"ncu_profile_step": wl.name, "launches": plan.kernel_launches(True) + 1}), flush=True)
+        return
     if args.expm_kernel == "tc":
         plan.set_expm_rules([(112, 2, 0)])      # tcgen05 tensor cores where the block fits
     elif args.expm_kernel == "tiled":
@@ -575,6 +587,9 @@ def build_parser():
     ap.add_argument("--prec", choices=["default", "f64", "f32", "f32_all"], default="default",
                     help="override the workload's precision")
     ap.add_argument("--autotune", action="store_true", help="tune the exponential kernels before timing")
+    ap.add_argument("--ncu", action="store_true",
+                    help="profiling mode: run one step of the workload and exit (for ncu launch lists and captures)")
+    ap.add_argument("--sn-problems", type=int, default=0, help="problems of the sn-batch workload (default 256)")
     ap.add_argument("--expm-kernel", choices=["default", "tiled", "tc"], default="default",
                     help="force the exponential kernel: tiled CUDA-core or tcgen05 tensor-core")
     ap.add_argument("--ws-train", type=int, default=WS_TRAIN, help="warm-start training problems")
@@ -587,7 +602,7 @@ def main():
     if args.steps is None:
         wl_cls = WORKLOADS.get(args.workload)
         args.steps = wl_cls.default_steps if wl_cls is not None else 1
-    args.warmup = max(args.warmup, 3) if args.impl == "ours" else args.warmup
+    args.warmup = max(args.warmup, 3) if args.impl == "ours" and not args.ncu else args.warmup
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if world > 1 and args.impl == "ours":

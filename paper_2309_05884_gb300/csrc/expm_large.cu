@@ -7,8 +7,8 @@
 // chunk of slices in a global scratch area.
 //   xl_prep      per slice: norm bound, Taylor degree, power-of-two operand scales, ownership (slices
 //                that need squarings are left to the CUDA-core tiles);
-//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j) in FP32, and the split operand planes of X (both
-//                sides) and of S = c_{2q-1} X + c_{2q-2} I;
+//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j) in FP32, and the split operand planes of X and of
+//                S = c_{2q-1} X + c_{2q-2} I;
 //   xl_gemm      Y^T = X^T X^T, then S <- S Y + c_{2j+1} X + c_{2j} I for j = q-2 .. 0; the last step
 //                writes U = T(X) into the propagator store;
 //   xl_export    U = I + X for the slices of degree 1.
@@ -22,7 +22,9 @@
 // transposed, so that its B-side slabs are written as rows like every other output.  The (hi, hi)
 // products accumulate in one pair of TMEM accumulators and the three smaller split products in
 // another, added in FP32 at the end: with K up to 2048 the small terms are never rounded against the
-// large running sum.
+// large running sum.  X is anti-Hermitian (H is Hermitian), so X^T = -conj(X): the rows of X^T that the
+// first product reads as its A operand are the A-side planes of X with the real planes negated, which
+// that product applies through the MMA's negate bits instead of storing a second copy of X.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -98,18 +100,17 @@ __device__ __forceinline__ bool xl_put8(unsigned char* slab, int off, const floa
     return ok;
 }
 
-// Scratch of one slice: X in FP32 [m][m] (xbytes), then five plane sets of pbytes each.
+// Scratch of one slice: X in FP32 [m][m] (xbytes), then four plane sets of pbytes each.
 struct XlMats {
     float2* X;
-    unsigned char *XA, *XB, *YT, *S0, *S1;  // X (A side), X (B side), Y (B side) = Y^T (A side), S ping-pong
+    unsigned char *XA, *YT, *S0, *S1;  // X (A side), Y (B side) = Y^T (A side), S ping-pong
 };
 __device__ __forceinline__ XlMats xl_mats(unsigned char* scratch, int slice, size_t xbytes, size_t pbytes) {
-    unsigned char* b = scratch + (size_t)slice * (xbytes + 5 * pbytes);
+    unsigned char* b = scratch + (size_t)slice * (xbytes + 4 * pbytes);
     XlMats M;
     M.X = reinterpret_cast<float2*>(b);
     M.XA = b + xbytes;
-    M.XB = M.XA + pbytes;
-    M.YT = M.XB + pbytes;
+    M.YT = M.XA + pbytes;
     M.S0 = M.YT + pbytes;
     M.S1 = M.S0 + pbytes;
     return M;
@@ -165,11 +166,10 @@ __global__ void xl_prep_kernel(DevPlan P, ExpmTables tabs, const double* __restr
 }
 
 // For every owned slice (grid: chunks of groups, slice): X = -i sc (H0 + sum_j u_j Hc_j) in FP32 and
-// the planes of X on both sides (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I on the A
-// side (scale 2^eS, in S1 where the first Horner step reads it), zero outside the m x m block.  A
-// group is eight consecutive K entries of one slab row: first the A-side groups (row r, entries
-// (r, 8g..8g+7)), then the B-side ones (row n of X^T, entries X[8g..8g+7][n]; n runs fastest so
-// that the column reads of H coalesce).
+// the A-side planes of X (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I (scale 2^eS,
+// in S1 where the first Horner step reads it), zero outside the m x m block.  A group is eight
+// consecutive K entries (r, 8g..8g+7) of one slab row; the row runs fastest, so that eight
+// consecutive threads fill one 128-byte core matrix of every plane.
 __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __restrict__ items,
                                    unsigned char* __restrict__ scratch, size_t xbytes, size_t pbytes) {
     const XlItem& X = items[blockIdx.y];
@@ -199,11 +199,11 @@ __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, cons
     };
     const long long G = (long long)mp * ng;
     bool ok = true;
-    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < 2 * G;
+    for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < G;
          idx += (long long)gridDim.x * blockDim.x) {
         float2 v[8];
-        if (idx < G) {
-            const int r = (int)(idx / ng), g = (int)(idx - (long long)r * ng);
+        {
+            const int g = (int)(idx / mp), r = (int)(idx - (long long)g * mp);
 #pragma unroll
             for (int c = 0; c < 8; ++c) v[c] = xval(r, 8 * g + c);
             if (r < m)
@@ -221,12 +221,6 @@ __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, cons
                 }
                 ok = xl_put8(M.S1 + sl, off, v, sS) && ok;
             }
-        } else {
-            const long long i2 = idx - G;
-            const int g = (int)(i2 / mp), n = (int)(i2 - (long long)g * mp);
-#pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = xval(8 * g + c, n);
-            ok = xl_put8(M.XB + xl_slab(n / XL_TM, (8 * g) / XL_KC, mp), xl_off(n % XL_TM, (8 * g) % XL_KC), v, sX) && ok;
         }
     }
     if (!ok) atomicOr(P.status, ST_RANGE);
@@ -234,7 +228,9 @@ __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, cons
 
 // One thread: the MMAs of one staged chunk.  Corrections (lo lo, hi lo, lo hi) into (cre, cim), the
 // (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
-__device__ __forceinline__ void xl_issue(uint32_t st, bool first, uint32_t hre, uint32_t him, uint32_t cre, uint32_t cim) {
+// nre: the A operand's real planes hold -Re(A) (negate the products that read them).
+__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, uint32_t hre, uint32_t him, uint32_t cre,
+                                         uint32_t cim) {
     const uint32_t lbo = 128, sbo = (XL_KC / 8) * 128;
     const uint32_t pos = idesc_f16(XL_TM, XL_TM, false), neg = idesc_f16(XL_TM, XL_TM, true);
     const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + XL_SLAB, lbo, sbo);
@@ -249,8 +245,8 @@ __device__ __forceinline__ void xl_issue(uint32_t st, bool first, uint32_t hre, 
         for (int kk = 0; kk < XL_KC / 16; ++kk) {
             const uint64_t s = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
             const int acc = !(first && kk == 0 && (t == 0 || t == 3));
-            mma_f16(dre, ar0 + s, br0 + s, pos, acc);
-            mma_f16(dim, ar0 + s, bi0 + s, pos, acc);
+            mma_f16(dre, ar0 + s, br0 + s, nre ? neg : pos, acc);
+            mma_f16(dim, ar0 + s, bi0 + s, nre ? neg : pos, acc);
             mma_f16(dre, ai0 + s, bi0 + s, neg, 1);
             mma_f16(dim, ai0 + s, br0 + s, pos, 1);
         }
@@ -258,8 +254,9 @@ __device__ __forceinline__ void xl_issue(uint32_t st, bool first, uint32_t hre, 
 }
 
 // One product for every owned slice of degree q >= 2 in the chunk: grid (128 x 128 output tiles of
-// the largest block, slice).  mode 0: Y^T = X^T X^T (A = X B side, B = X A side), written as the A
-// side of Y^T, i.e. the B side of Y, at scale 2^eY.  mode 1: Horner step j (slices with j <= q - 2):
+// the largest block, slice).  mode 0: Y^T = X^T X^T (A = rows of X^T = -conj(X): the A-side planes of
+// X with the real parts negated; B = X A side), written as the A side of Y^T, i.e. the B side of Y,
+// at scale 2^eY.  mode 1: Horner step j (slices with j <= q - 2):
 // S_out = S_in Y + c_{2j+1} X + c_{2j} I from S[(q-1-j) & 1] into S[(q-2-j) & 1] at scale 2^eS, or
 // for j = 0 into the propagator store U_b[kw] (FP32, m x m).
 __global__ void __launch_bounds__(XL_THREADS, 1)
@@ -283,7 +280,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
     unsigned char* Opl = nullptr;
     float unscale, sout = 1.f, c1 = 0.f, c0 = 0.f;
     if (mode == 0) {
-        Apl = M.XB;
+        Apl = M.XA;  // read as -conj(X) rows: the real planes are negated in xl_issue
         Bpl = M.XA;
         Opl = M.YT;
         unscale = ldexpf(1.f, -2 * X.eX);
@@ -340,7 +337,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
             }
             consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + st * XL_STAGE, ch == 0, hre, him, cre, cim);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, mode == 0, hre, him, cre, cim);
             mma_commit(&empty[st]);
             // refill the stage of chunk ch - 1 (its MMAs were queued before these) with chunk ch - 1 + S
             if (ch >= 1 && issued < nch) {
@@ -434,10 +431,10 @@ __global__ void xl_export_kernel(DevPlan P, const XlItem* __restrict__ items, un
 }  // namespace
 
 namespace {
-// bytes of one slice's scratch: X in FP32, then five plane sets of the padded size
+// bytes of one slice's scratch: X in FP32, then four plane sets of the padded size
 size_t xl_xbytes(int m_max) { return ((size_t)m_max * m_max * sizeof(float2) + 1023) / 1024 * 1024; }
 size_t xl_pbytes(int m_max) { return (size_t)8 * xl_pad(m_max) * xl_pad(m_max); }
-size_t xl_item_bytes(int m_max) { return xl_xbytes(m_max) + 5 * xl_pbytes(m_max); }
+size_t xl_item_bytes(int m_max) { return xl_xbytes(m_max) + 4 * xl_pbytes(m_max); }
 
 // slices per chunk: scratch of at most ~2 GiB, at most 256 slices, at least one
 long long xl_chunk(int m_max, long long max_items) {
@@ -471,7 +468,7 @@ int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u,
     // the highest degree a slice without squarings can need (its norm is at most theta_cap)
     int qmax = 1;
     while (qmax < 16 && tabs.theta_odd[qmax - 1] < tabs.theta_cap) ++qmax;
-    const long long groups = 2LL * xl_pad(m_max) * (xl_pad(m_max) / 8);
+    const long long groups = (long long)xl_pad(m_max) * (xl_pad(m_max) / 8);
     const int as_blocks = (int)std::min<long long>(64, (groups + 255) / 256);
     const int ew_blocks = (int)std::min<size_t>(64, ((size_t)m_max * m_max + 255) / 256);
     float2* U = reinterpret_cast<float2*>(Uout);
