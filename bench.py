@@ -44,6 +44,9 @@ EPS = 0.5          # GRAPE step
 SEED_U, SEED_PSI0, SEED_PSIF = 1, 101, 102
 FP32_PEAK_NOTE = "FP32 FMA peak = 152 SMs x 128 lanes x 2 flop x 2.07 GHz (max SM clock) = 80.5 TFLOP/s"
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# FP64 on GB300: 1.25 TFLOP/s nominal = 152 SMs x 2 FP64 FMA per clock x 2 flop x 2.07 GHz
+FP64_PEAK_NOTE = "FP64 FMA peak = 152 SMs x 2 lanes x 2 flop x 2.07 GHz (max SM clock) = 1.26 TFLOP/s"
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
 
 
 def measured_peaks(long_step: bool = False):
@@ -493,9 +496,12 @@ def run_ours(args, rank, world):
             "peak": tc_peak / 4, "frac": roofs["expm"]["achieved"] / (tc_peak / 4),
             "note": "algorithmic rate of a split-FP16 kernel with the tensor pipe always busy"}
     else:
-        roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles)",
-                         "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
-                         "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_step": expm_flop}
+        f64 = wl.prec == "f64"
+        roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles, %s)" % ("FP64" if f64 else "FP32"),
+                         "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12,
+                         "peak": FP64_PEAK_TFLOPS if f64 else FP32_PEAK_TFLOPS,
+                         "unit": "TFLOP/s", "peak_source": FP64_PEAK_NOTE if f64 else FP32_PEAK_NOTE,
+                         "flops_per_step": expm_flop}
     grad_flop = 8.0 * counts[3] / n
     if grad_flop > 0:
         roofs["slice_derivatives"] = {
