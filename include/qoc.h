@@ -305,6 +305,19 @@ int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
 int qoc_plan_set_deriv_gemm(qoc_plan* plan, int on);
 int qoc_plan_deriv_gemm(const qoc_plan* plan, int* blocks);
 
+/* One persistent launch per iteration (FP64 plans without checkpointing, exact derivative): on = 1
+ * makes qoc_fidelity_and_grad and every iteration of qoc_optimize_pulses a single cooperative kernel
+ * launch (preceded by a 16-byte memset of its counters) over all problems and blocks: norm check and
+ * gathers, propagators (Eq. exppropagator), forward states and costates, overlaps (Eq. probability),
+ * slice derivatives (Appendix B; reverse mode through the computed propagator for every slice), the
+ * gradient and the update rule, separated by grid barriers whose waits give up after 2 s (status
+ * QOC_ETIMEOUT).  Work inside a phase is handed out by atomic queues.  The workspace grows by one
+ * scratch slot per resident CTA: query qoc_plan_workspace_bytes again.  Graph replay
+ * (qoc_opt_opts.use_graph) captures the one launch.  Errors: QOC_EUNSUPPORTED (FP32 plan,
+ * checkpointing, first-order mode, blocks too large for the kernel's shared memory).  The qoc_fidelity_forward /
+ * qoc_fidelity_backward halves keep their own launches.  The paper has no counterpart. */
+int qoc_plan_set_persistent(qoc_plan* plan, int on);
+
 /* Kernel choice of the batched exponentials (Sec. II.A, Eq. exppropagator, as in qoc_expm_blocks):
  * rule i applies to blocks of size m <= m_max[i] (rules are tried in increasing m_max; the first
  * that applies wins): kind 0 = tiled CTA kernel, param = register tile R (1..7 FP32, 1..4 FP64; 0 =

@@ -93,6 +93,7 @@ SIGNATURES = {
     "qoc_plan_sweep_cluster": (C.c_int, [P, C.POINTER(C.c_int)]),
     "qoc_plan_set_deriv_gemm": (C.c_int, [P, C.c_int]),
     "qoc_plan_deriv_gemm": (C.c_int, [P, C.POINTER(C.c_int)]),
+    "qoc_plan_set_persistent": (C.c_int, [P, C.c_int]),
     "qoc_plan_expm_classes": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
                                         C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "qoc_dense_forward": (C.c_int, [P, P, P, P, P, C.c_longlong, C.c_int, C.c_int, C.c_int, P]),

@@ -383,6 +383,16 @@ class Plan:
         where it applies) or the per-slice series kernel (False)."""
         L.check(self.lib.qoc_plan_set_deriv_gemm(self.handle, int(on)), "qoc_plan_set_deriv_gemm")
 
+    def set_persistent(self, on: bool) -> None:
+        """One cooperative launch per evaluation / GRAPE iteration (FP64 plans without checkpointing);
+        reallocates the workspace if its size changes."""
+        L.check(self.lib.qoc_plan_set_persistent(self.handle, int(on)), "qoc_plan_set_persistent")
+        nbytes = C.c_size_t()
+        L.check(self.lib.qoc_plan_workspace_bytes(self.handle, C.byref(nbytes)), "qoc_plan_workspace_bytes")
+        if nbytes.value != self.workspace_bytes:
+            self.workspace_bytes = nbytes.value
+            self._ws = None
+
     def deriv_gemm_blocks(self) -> int:
         n = C.c_int()
         L.check(self.lib.qoc_plan_deriv_gemm(self.handle, C.byref(n)), "qoc_plan_deriv_gemm")

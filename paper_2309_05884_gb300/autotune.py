@@ -1,9 +1,14 @@
-"""Autotuner for the batched exponentials: per block-size bucket, time the candidate kernels (tiled
-CTA kernel with register tiles R, or the warp-packed kernel with 1..32/MP matrices per warp) on
-the plan's real work and keep the fastest, then cache the choice per GPU, precision and bucket.
-
-The timing is the device time of the exponential phase of qoc_fidelity_and_grad (CUDA events the
-library records on the call's stream), median of a few repetitions.
+"""Autotuner for a plan's kernel choices, timed on the plan's real work and cached per GPU, precision
+and block sizes:
+  - exponentials, per block-size bucket: tiled CTA kernel with register tiles R, warp-packed kernel
+    with 1..32/MP matrices per warp, tcgen05 kernel one CTA per slice (unsquared slices or all), tiled
+    tcgen05 GEMMs for large blocks;
+  - sweeps: one CTA per chain or thread-block clusters of 2..8 CTAs;
+  - slice derivatives of blocks above 128 states: tall GEMMs shared by a chunk's slices or the
+    per-slice series kernel.
+Each choice is timed by the device time of its own phase of qoc_fidelity_and_grad (CUDA events the
+library records around that phase's launches), median of a few repetitions; the choices are made in
+that order, each with the earlier ones applied.
 """
 from __future__ import annotations
 
@@ -36,8 +41,10 @@ def _candidates(m_max: int, prec: str) -> List[Tuple[int, int]]:
     rmax = 4 if prec == "f64" else 7
     r0 = max(1, min(rmax, -(-m_max // 16)))
     out = [(0, r) for r in sorted({max(1, r0 - 1), r0, min(rmax, r0 + 1)})]
-    if prec != "f64" and m_max <= 112:
-        out.append((2, 0))  # tcgen05 tensor cores
+    if prec == "f32" and m_max <= 112:
+        out += [(2, 0), (2, 1)]  # tcgen05, one CTA per slice: unsquared slices / every slice
+    if prec == "f32" and 24 < m_max <= 2048:
+        out.append((3, 0))  # tiled tcgen05 GEMMs
     warp_ok = prec != "f32" and m_max <= (16 if prec == "f64" else 32)
     if warp_ok:
         mp = 8 if m_max <= 8 else 16 if m_max <= 16 else 32
@@ -45,16 +52,20 @@ def _candidates(m_max: int, prec: str) -> List[Tuple[int, int]]:
     return out
 
 
-def _time_expm(plan, u, psi0, psif, reps: int) -> float:
+def _time_phase(plan, u, psi0, psif, reps: int, phase: int, want_grad: bool) -> float:
     plan.set_profiling(True)
     times = []
     for _ in range(reps + 1):
-        plan.fidelity_and_grad(u, psi0, psif, want_grad=False)
-        times.append(plan.phase_times()[0])
+        plan.fidelity_and_grad(u, psi0, psif, want_grad=want_grad)
+        times.append(plan.phase_times()[phase])
     plan.set_profiling(False)
     plan.sync_status()
     times = sorted(times[1:])
     return times[len(times) // 2]
+
+
+def _time_expm(plan, u, psi0, psif, reps: int) -> float:
+    return _time_phase(plan, u, psi0, psif, reps, 0, False)
 
 
 def tune_expm(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, reps: int = 3,
@@ -93,3 +104,75 @@ def tune_expm(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, rep
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
     return out
+
+
+def _cached(cache_path, key):
+    if cache_path and os.path.exists(cache_path):
+        with open(cache_path) as f:
+            return json.load(f).get(key)
+    return None
+
+
+def _store(cache_path, key, value):
+    if not cache_path:
+        return
+    cache = {}
+    if os.path.exists(cache_path):
+        with open(cache_path) as f:
+            cache = json.load(f)
+    cache[key] = value
+    with open(cache_path, "w") as f:
+        json.dump(cache, f, indent=1)
+
+
+def tune_sweeps(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, reps: int = 3,
+                cache_path: Optional[str] = None) -> Dict:
+    """Cluster size of the forward/backward sweeps (0 = one CTA per chain), timed on the sweep phase."""
+    key = f"sweeps|{torch.cuda.get_device_name()}|{plan.prec}|{plan.n_prob}|" + ",".join(map(str, _block_sizes(plan)))
+    hit = _cached(cache_path, key)
+    if hit is not None:
+        plan.set_sweep_cluster(hit["cl"])
+        return dict(hit, cached=True)
+    trials = []
+    for cl in (0, 2, 3, 4, 6, 8):
+        try:
+            plan.set_sweep_cluster(cl)
+        except RuntimeError:
+            continue  # the cluster's buffers do not fit
+        trials.append({"cl": cl, "ms": _time_phase(plan, u, psi0, psif, reps, 1, True)})
+    best = min(trials, key=lambda t: t["ms"])
+    plan.set_sweep_cluster(best["cl"])
+    out = {"cl": best["cl"], "trials": trials}
+    _store(cache_path, key, out)
+    return dict(out, cached=False)
+
+
+def tune_derivatives(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, reps: int = 3,
+                     cache_path: Optional[str] = None) -> Dict:
+    """Large-block slice derivatives: tall GEMMs or the per-slice series kernel, timed on that phase."""
+    plan.set_deriv_gemm(True)
+    if plan.deriv_gemm_blocks() == 0:
+        return {"gemm": False, "trials": [], "cached": False, "applies": False}
+    key = f"deriv|{torch.cuda.get_device_name()}|{plan.prec}|" + ",".join(map(str, _block_sizes(plan)))
+    hit = _cached(cache_path, key)
+    if hit is not None:
+        plan.set_deriv_gemm(hit["gemm"])
+        return dict(hit, cached=True)
+    trials = []
+    for on in (True, False):
+        plan.set_deriv_gemm(on)
+        trials.append({"gemm": on, "ms": _time_phase(plan, u, psi0, psif, reps, 3, True)})
+    best = min(trials, key=lambda t: t["ms"])
+    plan.set_deriv_gemm(best["gemm"])
+    out = {"gemm": best["gemm"], "trials": trials}
+    _store(cache_path, key, out)
+    return dict(out, cached=False)
+
+
+def tune(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, reps: int = 3,
+         cache_path: Optional[str] = None) -> Dict:
+    """Every choice in turn: exponentials, sweeps, derivatives.  The plan's workspace size may change
+    (the Python Plan reallocates it)."""
+    return {"expm": tune_expm(plan, u, psi0, psif, reps, cache_path),
+            "sweeps": tune_sweeps(plan, u, psi0, psif, reps, cache_path),
+            "derivatives": tune_derivatives(plan, u, psi0, psif, reps, cache_path)}

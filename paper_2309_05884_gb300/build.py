@@ -19,7 +19,7 @@ LIB = os.path.join(HERE, "libqoc.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
           "-I", os.path.join(ROOT, "include"), "--expt-relaxed-constexpr"]
-SOURCES = ["basis.cpp", "plan.cu", "expm.cu", "sweep.cu", "grad.cu", "expm_static.cu", "expm_warp.cu", "grad_rev.cu", "mlp.cu", "tc_gemm.cu", "expm_tc.cu", "grad_fast.cu", "sweep_cluster.cu", "expm_large.cu", "grad_gemm.cu", "trotter.cu"]
+SOURCES = ["basis.cpp", "plan.cu", "expm.cu", "sweep.cu", "grad.cu", "expm_static.cu", "expm_warp.cu", "grad_rev.cu", "mlp.cu", "tc_gemm.cu", "expm_tc.cu", "grad_fast.cu", "sweep_cluster.cu", "expm_large.cu", "grad_gemm.cu", "trotter.cu", "persistent.cu"]
 
 
 def nvcc() -> str:

@@ -72,6 +72,16 @@ int launch_grad_gemm(const DevPlan& P, const double* u, const void* psi_store, c
                      const GgBlock* gb, int ngb, const int4* tiles, int ntiles, int S, int* aux, void* scratch,
                      cudaStream_t st);
 
+// ---- persistent.cu (one GRAPE iteration of an FP64 plan in one cooperative launch)
+int persistent_config(int max_m, int max_c, int* grid, size_t* slot, size_t* smem);
+// u is read by the iteration and, with rule.kind >= 0, updated in place; sync: 4 device words (zeroed
+// here before the launch); ts: 8 device words of global-timer stamps
+int launch_persistent(const DevPlan& P, const ExpmTables& tabs, double* u, const double2* psi0, const double2* psif,
+                      const int64_t* prob_state, double* out3, double2* o_ws, double2* partial, double* grad,
+                      const UpdateRule& rule, void* U, void* psi_st, void* lam_st, void* fwd0, void* fwd1, void* bwd0,
+                      void* bwd1, char* scratch, size_t slot_bytes, int m_max, int want_grad, unsigned* sync,
+                      unsigned long long* ts, int grid, size_t smem, cudaStream_t st);
+
 // ---- expm_tc.cu (tcgen05 tensor cores, FP16-split products; FP32 plans, m <= 112)
 int expm_tc_supported(int prec, int m);
 int expm_tc_grid_limit(int m_max);

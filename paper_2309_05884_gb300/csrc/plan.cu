@@ -94,6 +94,12 @@ struct qoc_plan {
     std::vector<GgBlock> gg;
     int gg_S = 0, gg_ntiles = 0;
     bool gg_on = true;
+    // one persistent launch per iteration (FP64 plans without checkpointing)
+    bool pk_on = false;
+    mutable bool pk_last = false;  // the last call ran the persistent kernel (phase times from its stamps)
+    int pk_grid = 0;
+    size_t pk_slot = 0, pk_smem = 0;
+    unsigned long long* d_pk_ts = nullptr;
     size_t gg_bytes = 0;
     GgBlock* d_gg = nullptr;
     int4* d_gg_tiles = nullptr;
@@ -129,7 +135,7 @@ struct qoc_plan {
     // workspace layout (bytes)
     size_t off_U = 0, off_psi = 0, off_lam = 0, off_partial = 0, off_o = 0, off_out3 = 0, off_expm = 0,
            off_grad = 0, off_ckpt = 0, off_lamb = 0, off_adam = 0, off_iter = 0, off_reached = 0, off_rev = 0,
-           off_gg = 0, off_ggaux = 0;
+           off_gg = 0, off_ggaux = 0, off_pk = 0, off_pksync = 0;
     size_t el = 16;
     size_t ws_bytes = 0;
     int64_t u_elems = 0, s_elems = 0, part_rows = 0;
@@ -503,6 +509,8 @@ void layout_workspace(qoc_plan* p, int64_t u_elems, int64_t s_elems, int64_t par
     p->off_rev = off;     off = align_up(off + p->rev_slot * (size_t)p->rev_grid, 256);
     p->off_gg = off;      off = align_up(off + p->gg_bytes, 256);
     p->off_ggaux = off;   off = align_up(off + sizeof(int) * (32 + p->gg.size() * (size_t)p->gg_S), 256);
+    p->off_pk = off;      off = align_up(off + (p->pk_on ? p->pk_slot * (size_t)p->pk_grid : 0), 256);
+    p->off_pksync = off;  off = align_up(off + 64, 256);
     p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
     p->off_lamb = off;    off = align_up(off + (size_t)2 * p->vlen * el, 256);
     p->off_adam = off;    off = align_up(off + (size_t)2 * p->rows * p->nc * sizeof(double), 256);
@@ -518,10 +526,28 @@ UpdateRule no_update() {
     return r;
 }
 
+// The whole evaluation (and update) in one persistent launch (qoc_plan_set_persistent).
+int persistent_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3,
+                    double* grad, double* u_update, const UpdateRule& rule, char* w, cudaStream_t st) {
+    const bool want_grad = grad || u_update;
+    p->pk_last = !p->capturing;
+    if (launch_persistent(p->dev(), p->tabs, u_update ? u_update : const_cast<double*>(u),
+                          reinterpret_cast<const double2*>(psi0), reinterpret_cast<const double2*>(psif),
+                          p->d_prob_state, out3, reinterpret_cast<double2*>(w + p->off_o),
+                          reinterpret_cast<double2*>(w + p->off_partial), grad, rule, w + p->off_U, w + p->off_psi,
+                          w + p->off_lam, ckpt_vec(p, w, 0), ckpt_vec(p, w, 1), lamb_vec(p, w, 0), lamb_vec(p, w, 1),
+                          w + p->off_pk, p->pk_slot, p->max_m, want_grad ? 1 : 0,
+                          reinterpret_cast<unsigned*>(w + p->off_pksync), p->d_pk_ts, p->pk_grid, p->pk_smem, st) != 0)
+        return cuda_fail(cudaGetLastError(), "persistent launch");
+    return QOC_OK;
+}
+
 // One F (+ gradient, + update) evaluation.  Without checkpointing the forward states and costates
 // run in one sweep launch; with it, the costate pass recomputes each segment's propagators.
 int fidelity_grad_impl(const qoc_plan* p, const double* u, const double* psi0, const double* psif, double* out3,
                        double* grad, double* u_update, const UpdateRule& rule, char* w, cudaStream_t st) {
+    if (p->pk_on) return persistent_impl(p, u, psi0, psif, out3, grad, u_update, rule, w, st);
+    p->pk_last = false;
     int rc;
     const DevPlan P = p->dev();
     sections_begin(p);
@@ -960,6 +986,7 @@ void qoc_plan_free(qoc_plan* p) {
     cudaFree(p->d_prob_block_off);
     cudaFree(p->d_gg);
     cudaFree(p->d_gg_tiles);
+    cudaFree(p->d_pk_ts);
     cudaFree(p->d_status);
     cudaFree(p->d_prob_state);
     if (p->h_status) cudaFreeHost(p->h_status);
@@ -1021,6 +1048,15 @@ int qoc_plan_set_profiling(qoc_plan* p, int on) {
 int qoc_plan_phase_times(qoc_plan* p, float* ms, int n) {
     if (!p || !ms) return set_error(QOC_EINVAL, "null argument");
     if (!p->profiling) return set_error(QOC_EINVAL, "profiling is off");
+    if (p->pk_last) {
+        cudaSetDevice(p->device);
+        unsigned long long t[8];
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = cudaMemcpy(t, p->d_pk_ts, sizeof(t), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return cuda_fail(e, "persistent phase stamps");
+        for (int i = 0; i < n && i < 5; ++i) ms[i] = (float)((double)(t[i + 2] - t[i + 1]) * 1e-6);
+        return QOC_OK;
+    }
     if (p->sec_phase.empty()) return set_error(QOC_EINVAL, "no call was timed since profiling was enabled");
     cudaSetDevice(p->device);
     const size_t last = 2 * p->sec_phase.size() - 1;
@@ -1063,6 +1099,10 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     }
     // register-tile derivative launch per gradient pass (FP32 plans), plus the GEMM path's chunks:
     // prep, load, (GG_PCAP + 1) GEMM + combine steps, contraction
+    if (p->pk_on && with_grad) {  // one cooperative launch (its counters are zeroed by a memset)
+        *launches = 1;
+        return QOC_OK;
+    }
     int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
     if (p->gg_on && !p->gg.empty() && p->opts.grad_mode == 0) {
         const int slots = p->nseg == 1 ? p->N : p->seg;
@@ -1098,6 +1138,40 @@ int qoc_plan_set_deriv_gemm(qoc_plan* p, int on) {
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
     }
+    return QOC_OK;
+}
+
+int qoc_plan_set_persistent(qoc_plan* p, int on) {
+    if (!p) return set_error(QOC_EINVAL, "null plan");
+    if (on != 0 && on != 1) return set_error(QOC_EINVAL, "on must be 0 or 1");
+    cudaSetDevice(p->device);
+    if (p->graph) {
+        cudaGraphExecDestroy(p->graph);
+        p->graph = nullptr;
+    }
+    if (!on) {
+        p->pk_on = false;
+        p->pk_last = false;
+        layout_workspace(p, p->u_elems, p->s_elems, p->part_rows);
+        return QOC_OK;
+    }
+    if (p->opts.prec != QOC_PREC_F64) return set_error(QOC_EUNSUPPORTED, "the persistent iteration runs FP64 plans");
+    if (p->nseg != 1) return set_error(QOC_EUNSUPPORTED, "the persistent iteration keeps every propagator (no checkpointing)");
+    if (p->opts.grad_mode != 0) return set_error(QOC_EUNSUPPORTED, "the persistent iteration computes the exact derivative");
+    int grid = 0;
+    size_t slot = 0, smem = 0;
+    if (!persistent_config(p->max_m, p->max_c, &grid, &slot, &smem))
+        return set_error(QOC_EUNSUPPORTED, "the persistent kernel's buffers do not fit in shared memory");
+    if (!p->d_pk_ts) {
+        cudaError_t e = cudaMalloc(&p->d_pk_ts, 8 * sizeof(unsigned long long));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc stamps");
+        cudaMemset(p->d_pk_ts, 0, 8 * sizeof(unsigned long long));
+    }
+    p->pk_grid = grid;
+    p->pk_slot = slot;
+    p->pk_smem = smem;
+    p->pk_on = true;
+    layout_workspace(p, p->u_elems, p->s_elems, p->part_rows);
     return QOC_OK;
 }
 
@@ -1213,7 +1287,7 @@ int qoc_fidelity_and_grad(const qoc_plan* p, const double* u, const double* psi0
     cudaSetDevice(p->device);
     cudaStream_t st = to_stream(stream);
     if ((rc = take_latched(p, st))) return rc;
-    if ((rc = check_norms(p, psi0, psif, st))) return rc;
+    if (!p->pk_on && (rc = check_norms(p, psi0, psif, st))) return rc;
     rc = fidelity_grad_impl(p, u, psi0, psif, out3, grad, nullptr, no_update(), static_cast<char*>(ws), st);
     if (rc == QOC_OK) record_status(p, st);
     return rc;
@@ -1228,6 +1302,7 @@ int qoc_fidelity_forward(const qoc_plan* p, const double* u, const double* psi0,
     cudaStream_t st = to_stream(stream);
     if ((rc = take_latched(p, st))) return rc;
     if ((rc = check_norms(p, psi0, psif, st))) return rc;
+    p->pk_last = false;
     rc = forward_impl(p, u, psi0, psif, out3, static_cast<char*>(ws), st);
     if (rc == QOC_OK) record_status(p, st);
     return rc;
@@ -1241,6 +1316,7 @@ int qoc_fidelity_backward(const qoc_plan* p, const double* u, const double* psif
     cudaSetDevice(p->device);
     cudaStream_t st = to_stream(stream);
     if ((rc = take_latched(p, st))) return rc;
+    p->pk_last = false;
     rc = backward_impl(p, u, psif, gF, grad, static_cast<char*>(ws), st);
     if (rc == QOC_OK) record_status(p, st);
     return rc;
@@ -1275,7 +1351,7 @@ int qoc_optimize_pulses(qoc_plan* p, double* u, const double* psi0, const double
     cudaStream_t st = to_stream(stream);
     if (o.use_graph && st == nullptr) return set_error(QOC_EINVAL, "graph replay needs a non-default stream");
     if ((rc = take_latched(p, st))) return rc;
-    if ((rc = check_norms(p, psi0, psif, st))) return rc;
+    if (!p->pk_on && (rc = check_norms(p, psi0, psif, st))) return rc;
     double* out3 = reinterpret_cast<double*>(w + p->off_out3);
     int* d_iter = reinterpret_cast<int*>(w + p->off_iter);
     int* d_reached = reached ? reached : reinterpret_cast<int*>(w + p->off_reached);

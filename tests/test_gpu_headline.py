@@ -193,3 +193,30 @@ def test_large_block_derivatives_gemm_path_matches_series_kernel(n, first, seg):
         F, o, gref = gr.fidelity_and_grad(prob, u.cpu().numpy(), s.tau)
         assert abs(o1[0] - F) <= TOL32
         assert np.linalg.norm(g1 - gref) / np.linalg.norm(gref) <= TOL32
+
+
+def test_autotuner_every_choice_keeps_results(tmp_path):
+    # D_11 (blocks of 126 and 186 states, FP32): exponential kinds per bucket, sweep cluster size and
+    # the derivative path are tuned and cached; results stay within the FP32 tolerance
+    from paper_2309_05884_gb300 import autotune
+    s = I.xxz_ring(11, 0.02 * 24, 24)
+    B = api.Basis(s)
+    b0 = B.state_to_blocks(I.random_state(331, 2 ** 11))
+    bf = B.state_to_blocks(I.random_state(332, 2 ** 11))
+    plan = api.Plan(B, s.N, s.tau, prec="f32", active=B.active_copies(b0, bf))
+    d0, df = api.to_device(b0, DEV), api.to_device(bf, DEV)
+    u = torch.from_numpy(I.pulses_normal(8, s.N, 3)).to(DEV)
+    o0, g0 = plan.fidelity_and_grad(u, d0, df)
+    o0, g0 = o0.cpu().numpy(), g0.cpu().numpy()
+    cache = str(tmp_path / "tune.json")
+    rep = autotune.tune(plan, u, d0, df, reps=2, cache_path=cache)
+    assert rep["expm"]["rules"] and len(rep["sweeps"]["trials"]) >= 2 and len(rep["derivatives"]["trials"]) == 2
+    o1, g1 = plan.fidelity_and_grad(u, d0, df)
+    torch.cuda.synchronize()
+    plan.sync_status()
+    o1, g1 = o1.cpu().numpy(), g1.cpu().numpy()
+    assert abs(o1[0] - o0[0]) <= 1e-5
+    assert np.linalg.norm(g1 - g0) / np.linalg.norm(g0) <= 1e-5
+    rep2 = autotune.tune(plan, u, d0, df, cache_path=cache)
+    assert rep2["expm"]["cached"] and rep2["sweeps"]["cached"] and rep2["derivatives"]["cached"]
+    assert rep2["sweeps"]["cl"] == rep["sweeps"]["cl"] and rep2["derivatives"]["gemm"] == rep["derivatives"]["gemm"]
