@@ -418,6 +418,9 @@ def run_ours(args, rank, world):
             print(json.dumps({"ncu_profile_step": wl.name, "launches": launches + (0 if launches == 1 else 2)}),
                   flush=True)
         return
+    if args.deriv != "default":
+        mode, min_m = {"off": (0, 0), "cuda": (1, 129), "tc": (2, 129), "tc-all": (2, 24)}[args.deriv]
+        plan.set_deriv_gemm(mode, min_m)
     if args.expm_kernel == "tc":
         plan.set_expm_rules([(112, 2, 0)])      # tcgen05 tensor cores where the block fits
     elif args.expm_kernel == "tiled":
@@ -597,6 +600,9 @@ def build_parser():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="d14")
     ap.add_argument("--prec", choices=["default", "f64", "f32", "f32_all"], default="default",
                     help="override the workload's precision")
+    ap.add_argument("--deriv", choices=["default", "off", "cuda", "tc", "tc-all"], default="default",
+                    help="slice-derivative path: per-slice series (off), tall GEMMs on CUDA cores or tensor cores for "
+                         "blocks above 128 states, or tensor cores for every block of 24 states or more")
     ap.add_argument("--autotune", action="store_true",
                     help="tune the exponential, sweep and derivative kernels before timing")
     ap.add_argument("--ncu", action="store_true",

@@ -294,15 +294,19 @@ int qoc_plan_set_sweep_cluster(qoc_plan* plan, int cl);
 /* Current cluster size of the sweeps (0: one CTA per chain). */
 int qoc_plan_sweep_cluster(const qoc_plan* plan, int* cl);
 
-/* Slice derivatives of large blocks (Appendix B, Eq. propagator_differentiation, exact form):
- * on = 1 (default for single-problem FP32 plans in exact mode) computes the derivative series of
- * every unsplit slice of blocks with more than 128 states as tall GEMMs shared by all slices of a
- * chunk: A_k x = -i tau (H0 x + sum_j u_kj Hc_j x) with H0, Hc_j the same for every slice, so one
- * step of the power chains of all slices is [H0; Hc_1; ...] times a matrix of their vectors, and the
- * Hc_j v products it yields are the ones the series contracts with.  on = 0 uses the per-slice series
- * kernel.  The results agree to rounding.  The paper has no counterpart: it is a choice of kernels.
+/* Slice derivatives as tall GEMMs (Appendix B, Eq. propagator_differentiation, exact form), for
+ * single-problem FP32 plans in exact mode: the derivative series of every unsplit slice of the blocks
+ * with at least min_m states runs as GEMMs shared by all slices of a chunk: A_k x = -i tau (H0 x +
+ * sum_j u_kj Hc_j x) with H0, Hc_j the same for every slice, so one step of the power chains of all
+ * slices is [H0; Hc_1; ...] times a matrix of their vectors, and the Hc_j v products it yields are the
+ * ones the series contracts with.  mode 0: off (per-slice series kernels); 1: FP32 CUDA-core tiles;
+ * 2 (default): tcgen05 tensor cores with both operands split into FP16 hi/lo planes (the products as
+ * in qoc_tc_cgemm, FP32 accumulation; the columns scaled per slice by the chain bound beta^p).
+ * min_m: 0 keeps the current threshold (default 129: smaller blocks use the register-tile kernel),
+ * else 8..4096.  The workspace size may change: query qoc_plan_workspace_bytes again.  The results
+ * agree to rounding.  The paper has no counterpart: it is a choice of kernels.
  * qoc_plan_deriv_gemm: number of blocks on the GEMM path (0 if off or none qualifies). */
-int qoc_plan_set_deriv_gemm(qoc_plan* plan, int on);
+int qoc_plan_set_deriv_gemm(qoc_plan* plan, int mode, int min_m);
 int qoc_plan_deriv_gemm(const qoc_plan* plan, int* blocks);
 
 /* One persistent launch per iteration (FP64 plans without checkpointing, exact derivative): on = 1

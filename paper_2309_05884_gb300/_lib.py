@@ -91,7 +91,7 @@ SIGNATURES = {
     "qoc_plan_set_expm_rules": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "qoc_plan_set_sweep_cluster": (C.c_int, [P, C.c_int]),
     "qoc_plan_sweep_cluster": (C.c_int, [P, C.POINTER(C.c_int)]),
-    "qoc_plan_set_deriv_gemm": (C.c_int, [P, C.c_int]),
+    "qoc_plan_set_deriv_gemm": (C.c_int, [P, C.c_int, C.c_int]),
     "qoc_plan_deriv_gemm": (C.c_int, [P, C.POINTER(C.c_int)]),
     "qoc_plan_set_persistent": (C.c_int, [P, C.c_int]),
     "qoc_plan_expm_classes": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),

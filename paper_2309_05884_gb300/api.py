@@ -378,10 +378,18 @@ class Plan:
         chain, -1 the automatic choice."""
         L.check(self.lib.qoc_plan_set_sweep_cluster(self.handle, cl), "qoc_plan_set_sweep_cluster")
 
-    def set_deriv_gemm(self, on: bool) -> None:
-        """Large-block slice derivatives as tall GEMMs shared by a chunk's slices (True, the default
-        where it applies) or the per-slice series kernel (False)."""
-        L.check(self.lib.qoc_plan_set_deriv_gemm(self.handle, int(on)), "qoc_plan_set_deriv_gemm")
+    def set_deriv_gemm(self, mode, min_m: int = 0) -> None:
+        """Slice derivatives as tall GEMMs shared by a chunk's slices: mode 0 / False off (per-slice
+        series kernels), 1 FP32 CUDA cores, 2 / True tensor cores (the default); min_m: the smallest
+        block on the path (0 keeps the current threshold).  Reallocates the workspace if its size
+        changes."""
+        mode = 2 if mode is True else 0 if mode is False else int(mode)
+        L.check(self.lib.qoc_plan_set_deriv_gemm(self.handle, mode, int(min_m)), "qoc_plan_set_deriv_gemm")
+        nbytes = C.c_size_t()
+        L.check(self.lib.qoc_plan_workspace_bytes(self.handle, C.byref(nbytes)), "qoc_plan_workspace_bytes")
+        if nbytes.value != self.workspace_bytes:
+            self.workspace_bytes = nbytes.value
+            self._ws = None
 
     def set_persistent(self, on: bool) -> None:
         """One cooperative launch per evaluation / GRAPE iteration (FP64 plans without checkpointing);

@@ -4,8 +4,8 @@ and block sizes:
     with 1..32/MP matrices per warp, tcgen05 kernel one CTA per slice (unsquared slices or all), tiled
     tcgen05 GEMMs for large blocks;
   - sweeps: one CTA per chain or thread-block clusters of 2..8 CTAs;
-  - slice derivatives of blocks above 128 states: tall GEMMs shared by a chunk's slices or the
-    per-slice series kernel.
+  - slice derivatives: the per-slice series kernels, or tall GEMMs shared by a chunk's slices (FP32
+    CUDA cores or tensor cores) for the blocks above a size threshold.
 Each choice is timed by the device time of its own phase of qoc_fidelity_and_grad (CUDA events the
 library records around that phase's launches), median of a few repetitions; the choices are made in
 that order, each with the earlier ones applied.
@@ -149,22 +149,22 @@ def tune_sweeps(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, r
 
 def tune_derivatives(plan, u: torch.Tensor, psi0: torch.Tensor, psif: torch.Tensor, reps: int = 3,
                      cache_path: Optional[str] = None) -> Dict:
-    """Large-block slice derivatives: tall GEMMs or the per-slice series kernel, timed on that phase."""
-    plan.set_deriv_gemm(True)
-    if plan.deriv_gemm_blocks() == 0:
-        return {"gemm": False, "trials": [], "cached": False, "applies": False}
-    key = f"deriv|{torch.cuda.get_device_name()}|{plan.prec}|" + ",".join(map(str, _block_sizes(plan)))
+    """Slice-derivative path: per-slice series kernels, or tall GEMMs (FP32 CUDA cores or tensor cores)
+    for the blocks above a size threshold, timed on the derivative phase."""
+    key = f"deriv|{torch.cuda.get_device_name()}|{plan.prec}|{plan.n_prob}|" + ",".join(map(str, _block_sizes(plan)))
     hit = _cached(cache_path, key)
     if hit is not None:
-        plan.set_deriv_gemm(hit["gemm"])
+        plan.set_deriv_gemm(hit["mode"], hit["min_m"])
         return dict(hit, cached=True)
     trials = []
-    for on in (True, False):
-        plan.set_deriv_gemm(on)
-        trials.append({"gemm": on, "ms": _time_phase(plan, u, psi0, psif, reps, 3, True)})
+    for mode, min_m in ((0, 129), (1, 129), (2, 129), (2, 24)):
+        plan.set_deriv_gemm(mode, min_m)
+        if mode and plan.deriv_gemm_blocks() == 0:
+            continue  # no block that large: same as off
+        trials.append({"mode": mode, "min_m": min_m, "ms": _time_phase(plan, u, psi0, psif, reps, 3, True)})
     best = min(trials, key=lambda t: t["ms"])
-    plan.set_deriv_gemm(best["gemm"])
-    out = {"gemm": best["gemm"], "trials": trials}
+    plan.set_deriv_gemm(best["mode"], best["min_m"])
+    out = {"mode": best["mode"], "min_m": best["min_m"], "trials": trials}
     _store(cache_path, key, out)
     return dict(out, cached=False)
 

@@ -264,7 +264,7 @@ __device__ __forceinline__ void gf_item(const GfSmem& S, const DevPlan& P, const
 
 __global__ void __launch_bounds__(GF_THREADS, 1)
 grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, const float2* __restrict__ psi_st,
-                 const float2* __restrict__ lam_st, double2* __restrict__ partial) {
+                 const float2* __restrict__ lam_st, double2* __restrict__ partial, int gemm_min_m) {
     extern __shared__ __align__(16) unsigned char dsm[];
     GfSmem S;
     S.X = reinterpret_cast<float2*>(dsm);
@@ -317,7 +317,9 @@ grad_fast_kernel(DevPlan P, double tol, double theta, const double* __restrict__
             s_ul[threadIdx.x][j] = isfinite(x) ? (float)x : 0.f;
         }
         s_beta[threadIdx.x] = beta;
-        return P.grad_mode != 0 || slice_halvings(beta, theta, GF_SUB_MAX) == 0;
+        if (P.grad_mode != 0) return true;
+        // unsplit slices of blocks on the GEMM path (grad_gemm.cu) are not this launch's
+        return slice_halvings(beta, theta, GF_SUB_MAX) == 0 && !(gemm_min_m > 0 && Bw.m >= gemm_min_m);
     };
     for (long long lb = 0; cta_select(total, lb, want, s_list, &s_nl, s_wc); lb += blockDim.x) {
         const int nl = s_nl;
@@ -402,13 +404,13 @@ size_t gf_smem() { return (size_t)(GF_PM + 1) * (GF_NVM + GF_CG) * GF_VL * sizeo
 int grad_fast_max_m(int prec) { return prec == QOC_PREC_F64 ? 0 : 128; }
 
 int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
-                     int max_m, int grid, cudaStream_t st) {
+                     int max_m, int grid, cudaStream_t st, int gemm_min_m) {
     if (P.prec == QOC_PREC_F64 || P.nc > 8 || max_m < 1) return 0;
     const size_t sm = gf_smem();
     if (cudaFuncSetAttribute(grad_fast_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm) != cudaSuccess)
         return -1;
     grad_fast_kernel<<<grid, GF_THREADS, sm, st>>>(P, GF32_SERIES_TOL, 3.0, u, (const float2*)psi_store, (const float2*)lam_store,
-                                                   partial);
+                                                   partial, gemm_min_m);
     return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 

@@ -51,26 +51,45 @@ long long expm_large_launches(const ExpmTables& tabs, int m_max, long long total
 
 // ---- grad_fast.cu (exact slice derivatives, FP32, m <= 128, unsplit slices; A in registers)
 int grad_fast_max_m(int prec);
+// gemm_min_m > 0: unsplit slices of blocks with m >= gemm_min_m belong to the GEMM path (grad_gemm.cu)
 int launch_grad_fast(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
-                     int max_m, int grid, cudaStream_t st);
+                     int max_m, int grid, cudaStream_t st, int gemm_min_m = 0);
 
-// ---- grad_gemm.cu (exact slice derivatives of blocks with m >= grad_gemm_min_m(), FP32 plans, unsplit
-// slices: the series chains of every slice of a chunk as tall GEMMs with the stacked [H0; Hc_j])
+// ---- grad_gemm.cu (exact slice derivatives of the blocks on the GEMM path, FP32 plans, unsplit slices:
+// the series chains of every slice of a chunk as tall GEMMs with the stacked [H0; Hc_j])
 constexpr int GG_PCAP = 19;  // longest series (beta <= 3: beta^20 / 20! < 7.5e-9)
 struct GgBlock {
     int bi;          // active block index
     int m, c;        // size, active copies
     int ncol;        // 2 c S columns of the chunk layout
     long long x0, x1, y, z, w;  // complex offsets in the chunk scratch: X ping, X pong, Y, Z store, W store
+    // tensor-core GEMM: split-FP16 slabs of the stacked H (plan memory, byte offset hp, scale 2^eH) and
+    // of the columns X (chunk scratch, byte offset xp), per-column scale exponents at int offset cs
+    long long hp, xp, cs;
+    int rtc, ctc, kc, eH;  // row tiles of the stacked H, column tiles, K chunks of 32
 };
+enum { GG_OFF = 0, GG_CUDA = 1, GG_TC = 2 };
 int grad_gemm_min_m();
 // Offsets of every block for S slice slots per chunk, and the GEMM tile list (block, row tile, column
-// tile); returns the tile count, *elems the complex elements of the chunk scratch.
-int grad_gemm_layout(GgBlock* gb, int ngb, int nc, int S, int4* tiles, int max_tiles, size_t* elems);
-// aux: 32 + ngb * S ints of device scratch
+// tile) for the CUDA-core (tc = 0) or tensor-core (tc = 1) product; returns the tile count, *elems the
+// complex elements of the FP32 chunk scratch, *xbytes the bytes of the column slabs that follow it.
+int grad_gemm_layout(GgBlock* gb, int ngb, int nc, int S, int tc, int4* tiles, int max_tiles, size_t* elems,
+                     size_t* xbytes);
+// Slab layout of every block's stacked [H0; Hc_j] for the tensor-core path (host): fills hp, rtc, kc and
+// the scale exponent eH from hmax[g] (a bound on the block's largest |entry|); *hbytes the total;
+// launch_grad_gemm_hplanes writes the slabs.
+int grad_gemm_hplanes(GgBlock* gb, int ngb, int nc, const double* hmax, size_t* hbytes);
+// aux: 32 + 2 ngb S ints + the column scales of device scratch (grad_gemm_aux_ints); min_m: blocks below
+// it are skipped (the other kernels own their slices); mode GG_CUDA or GG_TC
+size_t grad_gemm_aux_ints(const GgBlock* gb, int ngb, int S);
+// xplanes: the column slabs (grad_gemm_layout's xbytes); hplanes: the stacked-H slabs (GG_TC only)
 int launch_grad_gemm(const DevPlan& P, const double* u, const void* psi_store, const void* lam_store, double2* partial,
                      const GgBlock* gb, int ngb, const int4* tiles, int ntiles, int S, int* aux, void* scratch,
-                     cudaStream_t st);
+                     void* xplanes, const void* hplanes, int mode, int min_m, cudaStream_t st);
+// Writes every block's stacked-H slabs (gb on the device, after grad_gemm_hplanes filled hp, rtc, kc, eH);
+// h_off: device [ngb] complex offsets of each block's H0 in the FP32 H.
+int launch_grad_gemm_hplanes(const GgBlock* gb, int ngb, int nc, const void* H32, const long long* h_off, void* hplanes,
+                             int* status, cudaStream_t st);
 
 // ---- persistent.cu (one GRAPE iteration of an FP64 plan in one cooperative launch)
 int persistent_config(int max_m, int max_c, int* grid, size_t* slot, size_t* smem);

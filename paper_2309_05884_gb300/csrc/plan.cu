@@ -91,9 +91,14 @@ struct qoc_plan {
     int rev_grid = 0;
     size_t rev_slot = 0;
     // GEMM-path slice derivatives of large blocks (single-problem FP32 plans)
-    std::vector<GgBlock> gg;
+    std::vector<GgBlock> gg;       // blocks on the path (m >= gg_min_m)
     int gg_S = 0, gg_ntiles = 0;
-    bool gg_on = true;
+    int gg_mode = GG_TC;           // GG_OFF, GG_CUDA (FP32 CUDA-core tiles) or GG_TC (tcgen05)
+    int gg_min_m = 129;
+    size_t gg_xbytes = 0;          // column slabs after the FP32 chunk scratch
+    size_t gg_aux = 0;             // ints of device aux
+    void* d_gg_hplanes = nullptr;  // stacked-H slabs (GG_TC)
+    long long* d_gg_hoff = nullptr;
     // one persistent launch per iteration (FP64 plans without checkpointing)
     bool pk_on = false;
     mutable bool pk_last = false;  // the last call ran the persistent kernel (phase times from its stamps)
@@ -342,8 +347,8 @@ int run_sweeps(const qoc_plan* p, char* ws, int k0, int nk, int dirs, const char
 int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaStream_t st) {
     Timed tm(p, PH_DERIV, st);
     const DevPlan P = p->dev(k0, nk);
-    const bool gon = p->gg_on && !p->gg.empty();
-    const int gmin = gon ? grad_gemm_min_m() : 0;
+    const bool gon = p->gg_mode != GG_OFF && !p->gg.empty();
+    const int gmin = gon ? p->gg_min_m : 0;
     const int g = launch_grad_partials(P, u, ws + p->off_psi, ws + p->off_lam,
                                        reinterpret_cast<double2*>(ws + p->off_partial), ws + p->off_grad,
                                        p->grad_slot, p->max_m, p->grad_grid, st, gmin);
@@ -352,10 +357,11 @@ int run_grad(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
     if (gon &&
         launch_grad_gemm(P, u, ws + p->off_psi, ws + p->off_lam, reinterpret_cast<double2*>(ws + p->off_partial),
                          p->d_gg, (int)p->gg.size(), p->d_gg_tiles, p->gg_ntiles, p->gg_S,
-                         reinterpret_cast<int*>(ws + p->off_ggaux), ws + p->off_gg, st) != 0)
+                         reinterpret_cast<int*>(ws + p->off_ggaux), ws + p->off_gg,
+                         ws + p->off_gg + align_up(p->gg_bytes, 1024), p->d_gg_hplanes, p->gg_mode, p->gg_min_m, st) != 0)
         return cuda_fail(cudaGetLastError(), "gradient launch (GEMM path)");
     if (launch_grad_fast(P, u, ws + p->off_psi, ws + p->off_lam, reinterpret_cast<double2*>(ws + p->off_partial),
-                         p->max_m, p->gf_grid, st) != 0)
+                         p->max_m, p->gf_grid, st, gmin) != 0)
         return cuda_fail(cudaGetLastError(), "gradient launch (register tiles)");
     if (P.grad_mode == 0) {
         // large-norm slices: reverse-mode kernel, one launch per size class with that class's tile
@@ -507,8 +513,8 @@ void layout_workspace(qoc_plan* p, int64_t u_elems, int64_t s_elems, int64_t par
     p->off_expm = off;    off = align_up(off + p->expm_scratch, 256);
     p->off_grad = off;    off = align_up(off + p->grad_slot * (size_t)p->grad_grid, 256);
     p->off_rev = off;     off = align_up(off + p->rev_slot * (size_t)p->rev_grid, 256);
-    p->off_gg = off;      off = align_up(off + p->gg_bytes, 256);
-    p->off_ggaux = off;   off = align_up(off + sizeof(int) * (32 + p->gg.size() * (size_t)p->gg_S), 256);
+    p->off_gg = off;      off = align_up(off + (p->gg.empty() ? 0 : align_up(p->gg_bytes, 1024) + p->gg_xbytes), 1024);
+    p->off_ggaux = off;   off = align_up(off + sizeof(int) * p->gg_aux, 256);
     p->off_pk = off;      off = align_up(off + (p->pk_on ? p->pk_slot * (size_t)p->pk_grid : 0), 256);
     p->off_pksync = off;  off = align_up(off + 64, 256);
     p->off_ckpt = off;    off = align_up(off + (size_t)(p->nseg + 1) * p->vlen * el, 256);
@@ -517,6 +523,75 @@ void layout_workspace(qoc_plan* p, int64_t u_elems, int64_t s_elems, int64_t par
     p->off_iter = off;    off = align_up(off + sizeof(int), 256);
     p->off_reached = off; off = align_up(off + (size_t)p->n_prob * sizeof(int), 256);
     p->ws_bytes = off;
+}
+
+// The GEMM path of the slice derivatives (grad_gemm.cu) for the plan's mode and threshold: blocks,
+// chunk size, layout, tile lists and (tensor cores) the stacked-H slabs.  Single-problem FP32 plans in
+// exact mode only; the workspace layout must be recomputed afterwards.
+int build_gg(qoc_plan* p) {
+    cudaFree(p->d_gg);
+    cudaFree(p->d_gg_tiles);
+    cudaFree(p->d_gg_hplanes);
+    cudaFree(p->d_gg_hoff);
+    p->d_gg = nullptr;
+    p->d_gg_tiles = nullptr;
+    p->d_gg_hplanes = nullptr;
+    p->d_gg_hoff = nullptr;
+    p->gg.clear();
+    p->gg_bytes = p->gg_xbytes = p->gg_aux = 0;
+    p->gg_S = p->gg_ntiles = 0;
+    if (p->opts.prec == QOC_PREC_F64 || p->opts.grad_mode != 0 || p->n_prob != 1 || p->gg_mode == GG_OFF) return QOC_OK;
+    std::vector<double> hmax;
+    std::vector<long long> hoff;
+    for (int bi = 0; bi < p->nb; ++bi)
+        if (p->hblocks[bi].m >= p->gg_min_m) {
+            GgBlock G{};
+            G.bi = bi;
+            G.m = p->hblocks[bi].m;
+            G.c = p->hblocks[bi].c;
+            p->gg.push_back(G);
+            const auto& blk = p->probs[0].basis->blocks[p->hblocks[bi].b];
+            double mx = 0.0;
+            for (const auto& z : blk.h0) mx = std::max(mx, std::max(std::fabs(z.real()), std::fabs(z.imag())));
+            for (const auto& z : blk.hc) mx = std::max(mx, std::max(std::fabs(z.real()), std::fabs(z.imag())));
+            hmax.push_back(mx);
+            hoff.push_back(p->hblocks[bi].h_off);
+        }
+    if (p->gg.empty()) return QOC_OK;
+    const int ngb = (int)p->gg.size();
+    const int tc = p->gg_mode == GG_TC;
+    // chunk slots: every slice of a window at once where about 1.5 GB of scratch allows, at most 512
+    const int slots = p->nseg == 1 ? p->N : p->seg;
+    size_t per_slot = 0;
+    for (const auto& G : p->gg)
+        per_slot += (size_t)G.c * G.m * sizeof(float2) * (4 + 2 * (1 + p->nc) + (GG_PCAP + 1) * (1 + p->nc)) +
+                    (size_t)2 * G.c * ((G.m + 31) / 32 * 32) * 8;  // column slabs: 4 FP16 planes
+    p->gg_S = (int)std::max<size_t>(1, std::min<size_t>({(size_t)slots, (size_t)512, ((size_t)3 << 29) / per_slot}));
+    size_t elems = 0;
+    if (tc) {
+        size_t hbytes = 0;
+        grad_gemm_hplanes(p->gg.data(), ngb, p->nc, hmax.data(), &hbytes);
+        cudaError_t e = cudaMalloc(&p->d_gg_hplanes, hbytes);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc H slabs");
+    }
+    p->gg_ntiles = grad_gemm_layout(p->gg.data(), ngb, p->nc, p->gg_S, tc, nullptr, 0, &elems, &p->gg_xbytes);
+    std::vector<int4> tl(p->gg_ntiles);
+    grad_gemm_layout(p->gg.data(), ngb, p->nc, p->gg_S, tc, tl.data(), p->gg_ntiles, &elems, &p->gg_xbytes);
+    p->gg_bytes = elems * sizeof(float2);
+    p->gg_aux = grad_gemm_aux_ints(p->gg.data(), ngb, p->gg_S);
+    cudaError_t e;
+    if ((e = cudaMalloc(&p->d_gg, sizeof(GgBlock) * ngb)) != cudaSuccess) return cuda_fail(e, "upload GEMM-path blocks");
+    cudaMemcpy(p->d_gg, p->gg.data(), sizeof(GgBlock) * ngb, cudaMemcpyHostToDevice);
+    if ((e = cudaMalloc(&p->d_gg_tiles, sizeof(int4) * tl.size())) != cudaSuccess) return cuda_fail(e, "upload GEMM-path tiles");
+    cudaMemcpy(p->d_gg_tiles, tl.data(), sizeof(int4) * tl.size(), cudaMemcpyHostToDevice);
+    if (tc) {
+        if ((e = cudaMalloc(&p->d_gg_hoff, sizeof(long long) * ngb)) != cudaSuccess) return cuda_fail(e, "upload H offsets");
+        cudaMemcpy(p->d_gg_hoff, hoff.data(), sizeof(long long) * ngb, cudaMemcpyHostToDevice);
+        if (launch_grad_gemm_hplanes(p->d_gg, ngb, p->nc, p->d_H, p->d_gg_hoff, p->d_gg_hplanes, p->d_status, nullptr) != 0)
+            return cuda_fail(cudaGetLastError(), "H slabs launch");
+        if ((e = cudaStreamSynchronize(nullptr)) != cudaSuccess) return cuda_fail(e, "H slabs");
+    }
+    return QOC_OK;
 }
 
 UpdateRule no_update() {
@@ -876,25 +951,6 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         p->rev_grid = (int)std::max<long long>(1, std::min<long long>({grad_items, (long long)sms, by_mem}));
     }
 
-    // large blocks' slice derivatives as tall GEMMs (single-problem FP32 plans, exact mode)
-    if (o.prec != QOC_PREC_F64 && o.grad_mode == 0 && n_problems == 1) {
-        for (int bi = 0; bi < p->nb; ++bi)
-            if (p->hblocks[bi].m >= grad_gemm_min_m()) {
-                GgBlock G{};
-                G.bi = bi;
-                G.m = p->hblocks[bi].m;
-                G.c = p->hblocks[bi].c;
-                p->gg.push_back(G);
-            }
-        if (!p->gg.empty()) {
-            const int slots = p->nseg == 1 ? Ns[0] : p->seg;
-            p->gg_S = std::min(64, slots);
-            size_t elems = 0;
-            p->gg_ntiles = grad_gemm_layout(p->gg.data(), (int)p->gg.size(), nc, p->gg_S, nullptr, 0, &elems);
-            p->gg_bytes = elems * sizeof(float2);
-        }
-    }
-
     // workspace layout
     p->u_elems = u_off;
     p->s_elems = s_off;
@@ -923,13 +979,6 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
     QOC_UP(p->d_prob_blocks, p->prob_blocks.data(), p->prob_blocks.size(), "upload problems");
     QOC_UP(p->d_prob_block_off, p->prob_block_off.data(), p->prob_block_off.size(), "upload problems");
     QOC_UP(p->d_H64, reinterpret_cast<double2*>(H64.data()), H64.size(), "upload H");
-    if (!p->gg.empty()) {
-        std::vector<int4> tl(p->gg_ntiles);
-        size_t elems = 0;
-        grad_gemm_layout(p->gg.data(), (int)p->gg.size(), nc, p->gg_S, tl.data(), p->gg_ntiles, &elems);
-        QOC_UP(p->d_gg, p->gg.data(), p->gg.size(), "upload GEMM-path blocks");
-        QOC_UP(p->d_gg_tiles, tl.data(), tl.size(), "upload GEMM-path tiles");
-    }
     {
         std::vector<int64_t> ps;
         for (const auto& pr : p->probs) {
@@ -960,6 +1009,14 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         cudaMemcpy(p->d_H, H32.data(), sizeof(float) * H32.size(), cudaMemcpyHostToDevice);
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return fail(e, "plan upload");
+    {
+        const int rc = build_gg(p);
+        if (rc) {
+            qoc_plan_free(p);
+            return rc;
+        }
+        layout_workspace(p, p->u_elems, p->s_elems, p->part_rows);
+    }
     *out = p;
     return QOC_OK;
 }
@@ -986,6 +1043,8 @@ void qoc_plan_free(qoc_plan* p) {
     cudaFree(p->d_prob_block_off);
     cudaFree(p->d_gg);
     cudaFree(p->d_gg_tiles);
+    cudaFree(p->d_gg_hplanes);
+    cudaFree(p->d_gg_hoff);
     cudaFree(p->d_pk_ts);
     cudaFree(p->d_status);
     cudaFree(p->d_prob_state);
@@ -1104,9 +1163,9 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
         return QOC_OK;
     }
     int gfl = (grad_fast_max_m(p->opts.prec) > 0 && p->nc <= 8) ? 1 : 0;
-    if (p->gg_on && !p->gg.empty() && p->opts.grad_mode == 0) {
+    if (p->gg_mode != GG_OFF && !p->gg.empty() && p->opts.grad_mode == 0) {
         const int slots = p->nseg == 1 ? p->N : p->seg;
-        gfl += ((slots + p->gg_S - 1) / p->gg_S) * (3 + 2 * (GG_PCAP + 1));
+        gfl += ((slots + p->gg_S - 1) / p->gg_S) * (3 + (p->gg_mode == GG_TC ? 3 : 2) * (GG_PCAP + 1));
     }
     if (p->nseg == 1)
         *launches = with_grad ? 2 + ncls + 1 + 1 + 1 + gfl + nrev + 1 : 1 + ncls + 1 + 1;
@@ -1129,15 +1188,26 @@ int qoc_plan_set_sweep_cluster(qoc_plan* p, int cl) {
     return QOC_OK;
 }
 
-int qoc_plan_set_deriv_gemm(qoc_plan* p, int on) {
+int qoc_plan_set_deriv_gemm(qoc_plan* p, int mode, int min_m) {
     if (!p) return set_error(QOC_EINVAL, "null plan");
-    if (on != 0 && on != 1) return set_error(QOC_EINVAL, "on must be 0 or 1");
-    p->gg_on = on != 0;
+    if (mode < GG_OFF || mode > GG_TC) return set_error(QOC_EINVAL, "mode must be 0 (off), 1 (CUDA cores) or 2 (tensor cores)");
+    if (min_m != 0 && (min_m < 8 || min_m > 4096)) return set_error(QOC_EINVAL, "min_m must be 0 (keep) or 8..4096");
+    cudaSetDevice(p->device);
     if (p->graph) {
-        cudaSetDevice(p->device);
         cudaGraphExecDestroy(p->graph);
         p->graph = nullptr;
     }
+    p->gg_mode = mode;
+    if (min_m) p->gg_min_m = min_m;
+    const int rc = build_gg(p);
+    if (rc) return rc;
+    layout_workspace(p, p->u_elems, p->s_elems, p->part_rows);
+    return QOC_OK;
+}
+
+int qoc_plan_deriv_gemm(const qoc_plan* p, int* blocks) {
+    if (!p || !blocks) return set_error(QOC_EINVAL, "null argument");
+    *blocks = p->gg_mode != GG_OFF ? (int)p->gg.size() : 0;
     return QOC_OK;
 }
 
@@ -1175,11 +1245,6 @@ int qoc_plan_set_persistent(qoc_plan* p, int on) {
     return QOC_OK;
 }
 
-int qoc_plan_deriv_gemm(const qoc_plan* p, int* blocks) {
-    if (!p || !blocks) return set_error(QOC_EINVAL, "null argument");
-    *blocks = p->gg_on ? (int)p->gg.size() : 0;
-    return QOC_OK;
-}
 
 int qoc_plan_sweep_cluster(const qoc_plan* p, int* cl) {
     if (!p || !cl) return set_error(QOC_EINVAL, "null argument");

@@ -1,0 +1,91 @@
+// Split-FP16 operand slabs and the MMA issue of the tiled tcgen05 GEMMs (expm_large.cu for the
+// large-block exponentials, grad_gemm.cu for the large-block slice derivatives).
+//
+// An operand matrix is kept as a grid of 32 KB slabs (128-row tile, 32-wide K chunk), each the four
+// FP16 planes re hi, re lo, im hi, im lo of its entries scaled by a power of two, in the K-major
+// no-swizzle core layout that the MMA descriptors read, so that one bulk copy moves a slab into
+// shared memory.  A complex product issues 16 kind::f16 MMAs per K step of 16: four real products for
+// each of the four split combinations; the (hi, hi) products accumulate in one pair of TMEM
+// accumulators and the three smaller ones in another, added in FP32 at the end, so the small terms
+// are never rounded against a long running sum.
+#pragma once
+
+#include <cuda_fp16.h>
+
+#include "tcgen05.cuh"
+
+namespace qoc {
+namespace {
+
+constexpr int XL_THREADS = 512;
+constexpr int XL_TM = 128, XL_KC = 32, XL_STAGES = 3;
+constexpr uint64_t XL_WAIT_NS = 2000000000ull;
+constexpr uint32_t XL_TMEM_COLS = 512;  // re, im of the (hi,hi) and of the correction accumulators
+constexpr uint32_t XL_PLANE = XL_TM * XL_KC * 2;  // bytes of one FP16 plane of a slab (8 KB)
+constexpr uint32_t XL_SLAB = 4 * XL_PLANE;        // one slab: four planes (32 KB)
+constexpr uint32_t XL_STAGE = 2 * XL_SLAB;        // one ring stage: an A slab and a B slab
+
+// one FP16 plane slab [rows][XL_KC] in the K-major no-swizzle core layout: element (row, k)
+__device__ __forceinline__ int xl_off(int row, int k) { return (((row >> 3) * (XL_KC >> 3) + (k >> 3)) << 6) + ((row & 7) << 3) + (k & 7); }
+
+__device__ __forceinline__ void xl_split(float x, __half& hi, __half& lo) {
+    hi = __float2half_rn(x);
+    lo = __float2half_rn(x - __half2float(hi));
+}
+
+// padded size of a block: whole 128-row tiles
+__host__ __device__ __forceinline__ int xl_pad(int m) { return (m + XL_TM - 1) / XL_TM * XL_TM; }
+
+// byte offset of slab (tile t, K chunk ch) in a plane set of padded size mp
+__device__ __forceinline__ size_t xl_slab(int t, int ch, int mp) {
+    return ((size_t)t * (mp / XL_KC) + ch) * XL_SLAB;
+}
+
+// Eight consecutive K entries v[0..8) of one slab row, scaled by s, split into the four planes at
+// halves offset off (a multiple of 8: 16 bytes per plane).  Returns false if a scaled entry leaves
+// the FP16 range.
+__device__ __forceinline__ bool xl_put8(unsigned char* slab, int off, const float2 (&v)[8], float s) {
+    __half h[4][8];
+    bool ok = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const float re = v[c].x * s, im = v[c].y * s;
+        ok = ok && fabsf(re) < 65504.f && fabsf(im) < 65504.f;
+        xl_split(re, h[0][c], h[1][c]);
+        xl_split(im, h[2][c], h[3][c]);
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint4*>(slab + p * XL_PLANE + off * 2) = *reinterpret_cast<const uint4*>(h[p]);
+    return ok;
+}
+
+// One thread: the MMAs of one staged chunk.  Corrections (lo lo, hi lo, lo hi) into (cre, cim), the
+// (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
+// nre: the A operand's real planes hold -Re(A) (negate the products that read them).
+__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, uint32_t hre, uint32_t him, uint32_t cre,
+                                         uint32_t cim) {
+    const uint32_t lbo = 128, sbo = (XL_KC / 8) * 128;
+    const uint32_t pos = idesc_f16(XL_TM, XL_TM, false), neg = idesc_f16(XL_TM, XL_TM, true);
+    const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + XL_SLAB, lbo, sbo);
+    const uint64_t pl = XL_PLANE >> 4;
+    const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};  // (lo,lo), (hi,lo), (lo,hi), (hi,hi)
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const uint32_t dre = t < 3 ? cre : hre, dim = t < 3 ? cim : him;
+        const uint64_t ar0 = dA + ha[t] * pl, ai0 = dA + (2 + ha[t]) * pl;
+        const uint64_t br0 = dB + hb[t] * pl, bi0 = dB + (2 + hb[t]) * pl;
+#pragma unroll
+        for (int kk = 0; kk < XL_KC / 16; ++kk) {
+            const uint64_t s = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
+            const int acc = !(first && kk == 0 && (t == 0 || t == 3));
+            mma_f16(dre, ar0 + s, br0 + s, nre ? neg : pos, acc);
+            mma_f16(dim, ar0 + s, bi0 + s, nre ? neg : pos, acc);
+            mma_f16(dre, ai0 + s, bi0 + s, neg, 1);
+            mma_f16(dim, ai0 + s, br0 + s, pos, 1);
+        }
+    }
+}
+
+}  // namespace
+}  // namespace qoc
