@@ -265,7 +265,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
             }
             consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + st * XL_STAGE, ch == 0, mode == 0, hre, him, cre, cim);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, mode == 0, false, hre, him, cre, cim);
             mma_commit(&empty[st]);
             // refill the stage of chunk ch - 1 (its MMAs were queued before these) with chunk ch - 1 + S
             if (ch >= 1 && issued < nch) {
@@ -378,50 +378,66 @@ int expm_large_supported(int prec, int m) { return prec != QOC_PREC_F64 && m >= 
 
 size_t expm_large_scratch_bytes(int m_max, long long max_items) {
     const long long ch = xl_chunk(m_max, max_items);
-    return xl_items_bytes(ch) + (size_t)ch * xl_item_bytes(m_max);
+    return xl_items_bytes(256) + (size_t)ch * xl_item_bytes(m_max);
 }
 
+// One block of the class at a time (its items are contiguous in the class's list), with chunks sized
+// to that block, so that the grid covers only its tiles.
 int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
-                      const int2* items, long long n_items, void* Uout, char* scratch, int m_max, cudaStream_t st) {
+                      const int2* items, long long n_items, void* Uout, char* scratch, int m_max, const int* hm,
+                      const long long* hcount, cudaStream_t st) {
     const long long total = P.nk < 0 ? n_items : (long long)n_cls * P.nk;
     if (total <= 0) return 0;
-    const long long ch = xl_chunk(m_max, total);
+    // the scratch holds ch_max slices of the class's largest block; a chunk of a smaller block fits more
+    const size_t budget = (size_t)xl_chunk(m_max, total) * xl_item_bytes(m_max);
     XlItem* it = reinterpret_cast<XlItem*>(scratch);
-    unsigned char* mats = reinterpret_cast<unsigned char*>(scratch + xl_items_bytes(ch));
-    const size_t xb = xl_xbytes(m_max), pb = xl_pbytes(m_max);
-    const int tiles = xl_pad(m_max) / XL_TM;
+    unsigned char* mats = reinterpret_cast<unsigned char*>(scratch + xl_items_bytes(256));
     const size_t smem = (size_t)XL_STAGES * XL_STAGE;
     if (cudaFuncSetAttribute(xl_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return -1;
-    // the highest degree a slice without squarings can need (its norm is at most theta_cap)
     int qmax = 1;
     while (qmax < 16 && tabs.theta_odd[qmax - 1] < tabs.theta_cap) ++qmax;
-    const long long groups = (long long)xl_pad(m_max) * (xl_pad(m_max) / 8);
-    const int as_blocks = (int)std::min<long long>(64, (groups + 255) / 256);
-    const int ew_blocks = (int)std::min<size_t>(64, ((size_t)m_max * m_max + 255) / 256);
     float2* U = reinterpret_cast<float2*>(Uout);
-    for (long long i0 = 0; i0 < total; i0 += ch) {
-        const int n = (int)std::min(ch, total - i0);
-        xl_prep_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, tabs, u, cls, items, i0, n, it);
-        xl_assemble_kernel<<<dim3(as_blocks, n), 256, 0, st>>>(P, u, it, mats, xb, pb);
-        if (qmax >= 2) {
-            xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 0, 0, U);
-            for (int j = qmax - 2; j >= 0; --j)
-                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 1, j, U);
+    long long i0b = 0;
+    for (int c = 0; c < n_cls; ++c) {
+        const int mb = hm[c];
+        const long long cnt = hcount[c];
+        const size_t xb = xl_xbytes(mb), pb = xl_pbytes(mb);
+        const long long ch = std::max(1LL, std::min<long long>({256LL, cnt, (long long)(budget / xl_item_bytes(mb))}));
+        const int tiles = xl_pad(mb) / XL_TM;
+        const long long groups = (long long)xl_pad(mb) * (xl_pad(mb) / 8);
+        const int as_blocks = (int)std::min<long long>(64, (groups + 255) / 256);
+        const int ew_blocks = (int)std::min<size_t>(64, ((size_t)mb * mb + 255) / 256);
+        for (long long i0 = i0b; i0 < i0b + cnt; i0 += ch) {
+            const int n = (int)std::min(ch, i0b + cnt - i0);
+            xl_prep_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, tabs, u, cls, items, i0, n, it);
+            xl_assemble_kernel<<<dim3(as_blocks, n), 256, 0, st>>>(P, u, it, mats, xb, pb);
+            if (qmax >= 2) {
+                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 0, 0, U);
+                for (int j = qmax - 2; j >= 0; --j)
+                    xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 1, j, U);
+            }
+            xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, xb, pb, U);
+            if (cudaGetLastError() != cudaSuccess) return -1;
         }
-        xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, xb, pb, U);
-        if (cudaGetLastError() != cudaSuccess) return -1;
+        i0b += cnt;
     }
     return 0;
 }
 
 // launches of one call: per chunk prep, assembly, Y, qmax - 1 Horner steps, export
-long long expm_large_launches(const ExpmTables& tabs, int m_max, long long total) {
-    if (total <= 0) return 0;
+long long expm_large_launches(const ExpmTables& tabs, int m_max, const int* hm, const long long* hcount, int n_cls) {
     int qmax = 1;
     while (qmax < 16 && tabs.theta_odd[qmax - 1] < tabs.theta_cap) ++qmax;
-    const long long ch = xl_chunk(m_max, total);
-    const long long chunks = (total + ch - 1) / ch;
+    long long total = 0;
+    for (int c = 0; c < n_cls; ++c) total += hcount[c];
+    if (total <= 0) return 0;
+    const size_t budget = (size_t)xl_chunk(m_max, total) * xl_item_bytes(m_max);
+    long long chunks = 0;
+    for (int c = 0; c < n_cls; ++c) {
+        const long long ch = std::max(1LL, std::min<long long>({256LL, hcount[c], (long long)(budget / xl_item_bytes(hm[c]))}));
+        chunks += (hcount[c] + ch - 1) / ch;
+    }
     return chunks * (3 + (qmax >= 2 ? qmax : 0));
 }
 

@@ -45,9 +45,12 @@ int launch_expm_warp(const DevPlan& P, const ExpmTables& tabs, const double* u, 
 // ---- expm_large.cu (tcgen05 tiled GEMMs for blocks of up to 2048 states, slices without squaring)
 int expm_large_supported(int prec, int m);
 size_t expm_large_scratch_bytes(int m_max, long long max_items);
+// hm, hcount (host, n_cls entries): size and item count of each class block, in the class's order
+// (its items are contiguous: a whole problem's slices, or nk window slices); one block at a time.
 int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u, const int* cls, int n_cls,
-                      const int2* items, long long n_items, void* Uout, char* scratch, int m_max, cudaStream_t st);
-long long expm_large_launches(const ExpmTables& tabs, int m_max, long long total);
+                      const int2* items, long long n_items, void* Uout, char* scratch, int m_max, const int* hm,
+                      const long long* hcount, cudaStream_t st);
+long long expm_large_launches(const ExpmTables& tabs, int m_max, const int* hm, const long long* hcount, int n_cls);
 
 // ---- grad_fast.cu (exact slice derivatives, FP32, m <= 128, unsplit slices; A in registers)
 int grad_fast_max_m(int prec);

@@ -82,6 +82,7 @@ struct qoc_plan {
     std::vector<int> prob_blocks, prob_block_off;
     ExpmTables tabs{};
     std::vector<ExpmClass> classes;
+    std::vector<int> h_cls;        // host copy of the class block lists
     std::vector<ExpmRule> rules;
     size_t expm_scratch = 0;
     int grad_grid = 0;
@@ -310,8 +311,15 @@ int run_expm(const qoc_plan* p, const double* u, char* ws, int k0, int nk, cudaS
             rc = launch_expm_warp(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                   c.R, c.per_warp, ws + p->off_U, c.grid, st);
         else if (c.kind == 3) {
+            std::vector<int> hm(c.count);
+            std::vector<long long> hcount(c.count);
+            for (int i = 0; i < c.count; ++i) {
+                const DevBlock& hb = p->hblocks[p->h_cls[c.offset + i]];
+                hm[i] = hb.m;
+                hcount[i] = nk < 0 ? hb.N : nk;
+            }
             rc = launch_expm_large(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
-                                   ws + p->off_U, ws + p->off_expm, c.m_max, st);
+                                   ws + p->off_U, ws + p->off_expm, c.m_max, hm.data(), hcount.data(), st);
             if (rc == 0)
                 rc = launch_expm(P, p->tabs, u, p->d_cls + c.offset, c.count, p->d_cls_items + c.item_off, c.n_items,
                                  c.R2, ws + p->off_U, ws + p->off_expm, c.slot2, c.m_max, c.grid2, st, 1);
@@ -496,6 +504,7 @@ int build_classes(qoc_plan* p) {
     if ((e = cudaMalloc(&p->d_cls_items, sizeof(int2) * std::max<size_t>(1, cls_items.size()))) != cudaSuccess)
         return cuda_fail(e, "upload classes");
     cudaMemcpy(p->d_cls, cls_list.data(), sizeof(int) * cls_list.size(), cudaMemcpyHostToDevice);
+    p->h_cls = cls_list;
     cudaMemcpy(p->d_cls_items, cls_items.data(), sizeof(int2) * cls_items.size(), cudaMemcpyHostToDevice);
     return QOC_OK;
 }
@@ -1150,8 +1159,14 @@ int qoc_plan_kernel_launches(const qoc_plan* p, int with_grad, int* launches) {
     int ncls = 0;                               // exponential launches per pass over all slices
     for (const auto& c : p->classes) {
         if (c.kind == 3) {
-            const long long per = p->nseg == 1 ? c.n_items : (long long)c.count * p->seg;
-            ncls += (int)expm_large_launches(p->tabs, c.m_max, per) + 1;
+            std::vector<int> hm(c.count);
+            std::vector<long long> hcount(c.count);
+            for (int i = 0; i < c.count; ++i) {
+                const DevBlock& hb = p->hblocks[p->h_cls[c.offset + i]];
+                hm[i] = hb.m;
+                hcount[i] = p->nseg == 1 ? hb.N : p->seg;
+            }
+            ncls += (int)expm_large_launches(p->tabs, c.m_max, hm.data(), hcount.data(), c.count) + 1;
         } else {
             ncls += (c.kind == 2 && c.R == 0) ? 2 : 1;
         }

@@ -62,14 +62,16 @@ __device__ __forceinline__ bool xl_put8(unsigned char* slab, int off, const floa
 
 // One thread: the MMAs of one staged chunk.  Corrections (lo lo, hi lo, lo hi) into (cre, cim), the
 // (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
-// nre: the A operand's real planes hold -Re(A) (negate the products that read them).
-__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, uint32_t hre, uint32_t him, uint32_t cre,
-                                         uint32_t cim) {
+// nre: the A operand's real planes hold -Re(A); nbre: the B operand's real planes hold -Re(B) (the
+// products that read them are negated).
+__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, bool nbre, uint32_t hre, uint32_t him,
+                                         uint32_t cre, uint32_t cim) {
     const uint32_t lbo = 128, sbo = (XL_KC / 8) * 128;
     const uint32_t pos = idesc_f16(XL_TM, XL_TM, false), neg = idesc_f16(XL_TM, XL_TM, true);
     const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + XL_SLAB, lbo, sbo);
     const uint64_t pl = XL_PLANE >> 4;
     const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};  // (lo,lo), (hi,lo), (lo,hi), (hi,hi)
+    const uint32_t s_rr = (nre != nbre) ? neg : pos, s_ri = nre ? neg : pos, s_ir = nbre ? neg : pos;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
         const uint32_t dre = t < 3 ? cre : hre, dim = t < 3 ? cim : him;
@@ -79,10 +81,10 @@ __device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, uint
         for (int kk = 0; kk < XL_KC / 16; ++kk) {
             const uint64_t s = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
             const int acc = !(first && kk == 0 && (t == 0 || t == 3));
-            mma_f16(dre, ar0 + s, br0 + s, nre ? neg : pos, acc);
-            mma_f16(dim, ar0 + s, bi0 + s, nre ? neg : pos, acc);
-            mma_f16(dre, ai0 + s, bi0 + s, neg, 1);
-            mma_f16(dim, ai0 + s, br0 + s, pos, 1);
+            mma_f16(dre, ar0 + s, br0 + s, s_rr, acc);  // Re += Ar Br
+            mma_f16(dim, ar0 + s, bi0 + s, s_ri, acc);  // Im += Ar Bi
+            mma_f16(dre, ai0 + s, bi0 + s, neg, 1);     // Re -= Ai Bi
+            mma_f16(dim, ai0 + s, br0 + s, s_ir, 1);    // Im += Ai Br
         }
     }
 }
