@@ -494,14 +494,20 @@ def run_ours(args, rank, world):
                          "flops_per_step": expm_flop,
                          "note": "algorithmic complex-FP32 flop (8 m^3 per product) over the summed durations of "
                                  "the exponential launches; the split issues 16 real FP16 products per complex "
-                                 "product on padded operands"
+                                 "product (12 in the Horner steps, which leave out lo*lo) on padded operands"
                                  + ("; checkpointed: every exponential is computed twice (forward pass and "
                                     "costate pass), both counted" if ckpt else "")}
-        # the split does 4 real FP16 products per real product, so a kernel that kept the tensor pipe
-        # busy all the time would reach a quarter of the peak in these algorithmic units
+        # a complex product is 4 real products of 4 (or, without lo*lo, 3) split FP16 products each:
+        # 32 m^3 (24 m^3) tensor flop per 8 m^3 algorithmic, so a kernel that kept the tensor pipe busy
+        # all the time would reach 1/4 (1/3) of the peak in these algorithmic units
+        prods = counts[0] + counts[1]
+        three = min(counts[5], prods)
+        ratio = 8.0 * prods / (32.0 * (prods - three) + 24.0 * three) if prods else 0.25
         roofs["expm"]["split_ceiling"] = {
-            "peak": tc_peak / 4, "frac": roofs["expm"]["achieved"] / (tc_peak / 4),
-            "note": "algorithmic rate of a split-FP16 kernel with the tensor pipe always busy"}
+            "peak": tc_peak * ratio, "frac": roofs["expm"]["achieved"] / (tc_peak * ratio),
+            "three_term_share": three / prods if prods else 0.0,
+            "note": "algorithmic rate of a split-FP16 kernel with the tensor pipe always busy, for this "
+                    "step's mix of four-term and three-term products"}
     else:
         f64 = wl.prec == "f64"
         roofs["expm"] = {"bound": "alu", "kernel": "expm_kernel (CUDA-core tiles, %s)" % ("FP64" if f64 else "FP32"),

@@ -358,7 +358,9 @@ int qoc_plan_expm_classes(const qoc_plan* plan, int max_out, int* n_classes, int
  * the (P+1)-term M tile, the contraction with each Hc_j); counts[4] = complex multiply-adds of the
  * slice-derivative series of large blocks done as tall GEMMs (FP32 plans, m > 128, unsplit slices):
  * per item (1 + n_ctrl) m^2 2c (P + 1) for the chains and c n_ctrl m (P + 1)(P + 2)/2 for the
- * contraction. */
+ * contraction; counts[5] = sum over (slice, block) items of m^3 times the tensor-core products taken
+ * with three split terms instead of four (the Horner steps; counts[0] + counts[1] - counts[5] of the
+ * tensor-core products keep all four). */
 int qoc_plan_set_profiling(qoc_plan* plan, int on);
 int qoc_plan_phase_times(qoc_plan* plan, float* ms_out, int n_out);
 int qoc_plan_work_counts(qoc_plan* plan, long long* counts_out, int n_out);

@@ -351,10 +351,10 @@ class Plan:
 
     def work_counts(self) -> List[int]:
         """[sum m^3 * polynomial products, sum m^3 * squarings, items, complex multiply-adds of the
-        register-tile derivative series, complex multiply-adds of the GEMM-path derivative series]
-        since profiling was enabled."""
-        out = (C.c_longlong * 5)()
-        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 5), "qoc_plan_work_counts")
+        register-tile derivative series, complex multiply-adds of the GEMM-path derivative series,
+        sum m^3 * tensor-core products taken with three split terms] since profiling was enabled."""
+        out = (C.c_longlong * 6)()
+        L.check(self.lib.qoc_plan_work_counts(self.handle, out, 6), "qoc_plan_work_counts")
         return list(out)
 
     def set_expm_rules(self, rules) -> None:

@@ -115,66 +115,91 @@ __global__ void xl_prep_kernel(DevPlan P, ExpmTables tabs, const double* __restr
             const unsigned long long m3 = (unsigned long long)B.m * B.m * B.m;
             atomicAdd(P.stats + 0, m3 * (unsigned long long)(q >= 2 ? q : 0));
             atomicAdd(P.stats + 2, 1ull);
+            if (q >= 2) atomicAdd(P.stats + 5, m3 * (unsigned long long)(q - 1));  // Horner: 3 split terms
         }
     }
     items[t] = X;
 }
 
-// For every owned slice (grid: chunks of groups, slice): X = -i sc (H0 + sum_j u_j Hc_j) in FP32 and
-// the A-side planes of X (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I (scale 2^eS,
-// in S1 where the first Horner step reads it), zero outside the m x m block.  A group is eight
-// consecutive K entries (r, 8g..8g+7) of one slab row; the row runs fastest, so that eight
-// consecutive threads fill one 128-byte core matrix of every plane.
-__global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __restrict__ items,
-                                   unsigned char* __restrict__ scratch, size_t xbytes, size_t pbytes) {
-    const XlItem& X = items[blockIdx.y];
-    if (!X.own) return;
-    const DevBlock& B = P.blocks[X.bi];
+// For every owned slice of the chunk (all of one block): X = -i sc (H0 + sum_j u_j Hc_j) in FP32, the
+// A-side planes of X (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I (scale 2^eS, in S1
+// where the first Horner step reads it), zero outside the m x m block.  A thread owns one group of
+// eight consecutive K entries (r, 8g..8g+7) of one slab row for every slice of the chunk: it reads
+// the block's H0 and Hc_j entries there once and writes them out, combined, slice after slice.  Rows
+// run fastest, so that eight consecutive threads fill one 128-byte core matrix of every plane.
+template <int NC>
+__global__ void __launch_bounds__(256, NC <= 3 ? 2 : 1)
+xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __restrict__ items, int n,
+                   unsigned char* __restrict__ scratch, size_t xbytes, size_t pbytes) {
+    __shared__ float s_u[256][NC];
+    __shared__ float s_sc[256], s_sX[256], s_sS[256], s_c1[256], s_c0[256];
+    __shared__ int s_q[256];  // 0: not owned; else the Horner count q
+    const DevBlock& B = P.blocks[items[0].bi];
     const int m = B.m, mp = xl_pad(m), ng = mp / 8;
     const size_t mm = (size_t)m * m;
     const float2* H = reinterpret_cast<const float2*>(P.H) + B.h_off;
-    float uf[8];
-    for (int j = 0; j < P.nc; ++j) {
-        const double x = u[(size_t)(B.u_row + X.k) * P.nc + j];
-        uf[j] = isfinite(x) ? (float)x : 0.f;
+    for (int e = threadIdx.x; e < n * NC; e += blockDim.x) {
+        const int t = e / NC, jc = e - t * NC;
+        const double x = u[(size_t)(B.u_row + items[t].k) * NC + jc];
+        s_u[t][jc] = isfinite(x) ? (float)x : 0.f;
     }
-    const XlMats M = xl_mats(scratch, blockIdx.y, xbytes, pbytes);
-    const float sX = ldexpf(1.f, X.eX), sS = ldexpf(1.f, X.eS);
-    const float c1 = xl_coef[2 * X.q - 1], c0 = xl_coef[2 * X.q - 2];
-    auto xval = [&](int r, int k) {  // X[r][k], 0 outside the block
-        if (r >= m || k >= m) return make_float2(0.f, 0.f);
-        const size_t e = (size_t)r * m + k;
-        float2 h = H[e];
-        for (int j = 0; j < P.nc; ++j) {
-            const float2 hc = H[(size_t)(1 + j) * mm + e];
-            h.x = fmaf(uf[j], hc.x, h.x);
-            h.y = fmaf(uf[j], hc.y, h.y);
-        }
-        return make_float2(h.y * X.sc, -h.x * X.sc);
-    };
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+        const XlItem X = items[t];
+        s_q[t] = X.own ? X.q : 0;
+        s_sc[t] = X.sc;
+        s_sX[t] = ldexpf(1.f, X.eX);
+        s_sS[t] = ldexpf(1.f, X.eS);
+        s_c1[t] = X.q >= 1 ? xl_coef[2 * X.q - 1] : 0.f;
+        s_c0[t] = X.q >= 1 ? xl_coef[2 * X.q - 2] : 0.f;
+    }
+    __syncthreads();
+    const size_t stride = xbytes + 4 * pbytes;  // one slice's scratch
     const long long G = (long long)mp * ng;
     bool ok = true;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < G;
          idx += (long long)gridDim.x * blockDim.x) {
-        float2 v[8];
-        {
-            const int g = (int)(idx / mp), r = (int)(idx - (long long)g * mp);
+        const int g = (int)(idx / mp), r = (int)(idx - (long long)g * mp);
+        float2 h[NC + 1][8];  // H0, Hc_1 .. Hc_NC at (r, 8g .. 8g+7), 0 outside the block
 #pragma unroll
-            for (int c = 0; c < 8; ++c) v[c] = xval(r, 8 * g + c);
-            if (r < m)
+        for (int jj = 0; jj <= NC; ++jj)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int k = 8 * g + c;
+                h[jj][c] = (r < m && k < m) ? H[(size_t)jj * mm + (size_t)r * m + k] : make_float2(0.f, 0.f);
+            }
+        const size_t pl = xl_slab(r / XL_TM, (8 * g) / XL_KC, mp) + (size_t)xl_off(r % XL_TM, (8 * g) % XL_KC) * 2;
+        const size_t xo = ((size_t)r * m + 8 * g) * sizeof(float2);
+        unsigned char* base = scratch;
+        for (int t = 0; t < n; ++t, base += stride) {
+            const int q = s_q[t];
+            if (!q) continue;
+            const float sc = s_sc[t];
+            float2 v[8];
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float2 a = h[0][c];
+#pragma unroll
+                for (int jc = 0; jc < NC; ++jc) {
+                    a.x = fmaf(s_u[t][jc], h[1 + jc][c].x, a.x);
+                    a.y = fmaf(s_u[t][jc], h[1 + jc][c].y, a.y);
+                }
+                v[c] = make_float2(a.y * sc, -a.x * sc);
+            }
+            if (r < m) {
+                float2* xr = reinterpret_cast<float2*>(base + xo);
 #pragma unroll
                 for (int c = 0; c < 8; ++c)
-                    if (8 * g + c < m) M.X[(size_t)r * m + 8 * g + c] = v[c];
-            const size_t sl = xl_slab(r / XL_TM, (8 * g) / XL_KC, mp);
-            const int off = xl_off(r % XL_TM, (8 * g) % XL_KC);
-            ok = xl_put8(M.XA + sl, off, v, sX) && ok;
-            if (X.q >= 2) {
+                    if (8 * g + c < m) xr[c] = v[c];
+            }
+            ok = xl_put8(base + xbytes + pl, 0, v, s_sX[t]) && ok;
+            if (q >= 2) {
+                const float c1 = s_c1[t], c0 = s_c0[t];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
                     v[c].x = c1 * v[c].x + (r == 8 * g + c && r < m ? c0 : 0.f);
                     v[c].y = c1 * v[c].y;
                 }
-                ok = xl_put8(M.S1 + sl, off, v, sS) && ok;
+                ok = xl_put8(base + xbytes + 3 * pbytes + pl, 0, v, s_sS[t]) && ok;
             }
         }
     }
@@ -186,7 +211,9 @@ __global__ void xl_assemble_kernel(DevPlan P, const double* __restrict__ u, cons
 // X with the real parts negated; B = X A side), written as the A side of Y^T, i.e. the B side of Y,
 // at scale 2^eY.  mode 1: Horner step j (slices with j <= q - 2):
 // S_out = S_in Y + c_{2j+1} X + c_{2j} I from S[(q-1-j) & 1] into S[(q-2-j) & 1] at scale 2^eS, or
-// for j = 0 into the propagator store U_b[kw] (FP32, m x m).
+// for j = 0 into the propagator store U_b[kw] (FP32, m x m).  Y = X X keeps the (lo, lo) products
+// (the lo parts of X and X^T are correlated); the Horner products, whose operands are different
+// matrices, leave them out.
 __global__ void __launch_bounds__(XL_THREADS, 1)
 xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch, size_t xbytes,
                size_t pbytes, int tiles_n, int mode, int j, float2* __restrict__ Uout) {
@@ -265,7 +292,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
             }
             consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + st * XL_STAGE, ch == 0, mode == 0, false, hre, him, cre, cim);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, mode == 0, false, mode == 0, hre, him, cre, cim);
             mma_commit(&empty[st]);
             // refill the stage of chunk ch - 1 (its MMAs were queued before these) with chunk ch - 1 + S
             if (ch >= 1 && issued < nch) {
@@ -406,12 +433,17 @@ int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u,
         const long long ch = std::max(1LL, std::min<long long>({256LL, cnt, (long long)(budget / xl_item_bytes(mb))}));
         const int tiles = xl_pad(mb) / XL_TM;
         const long long groups = (long long)xl_pad(mb) * (xl_pad(mb) / 8);
-        const int as_blocks = (int)std::min<long long>(64, (groups + 255) / 256);
+        const int as_blocks = (int)std::min<long long>(1024, (groups + 255) / 256);
         const int ew_blocks = (int)std::min<size_t>(64, ((size_t)mb * mb + 255) / 256);
         for (long long i0 = i0b; i0 < i0b + cnt; i0 += ch) {
             const int n = (int)std::min(ch, i0b + cnt - i0);
             xl_prep_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, tabs, u, cls, items, i0, n, it);
-            xl_assemble_kernel<<<dim3(as_blocks, n), 256, 0, st>>>(P, u, it, mats, xb, pb);
+            switch (P.nc) {
+#define XL_AS(K) case K: xl_assemble_kernel<K><<<as_blocks, 256, 0, st>>>(P, u, it, n, mats, xb, pb); break;
+                XL_AS(1) XL_AS(2) XL_AS(3) XL_AS(4) XL_AS(5) XL_AS(6) XL_AS(7) XL_AS(8)
+#undef XL_AS
+                default: return -1;
+            }
             if (qmax >= 2) {
                 xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 0, 0, U);
                 for (int j = qmax - 2; j >= 0; --j)

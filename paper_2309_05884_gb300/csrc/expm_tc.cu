@@ -115,7 +115,9 @@ __device__ __forceinline__ void ld_acc8(uint32_t t_re, uint32_t t_im, float (&re
 }
 
 // One thread: D(re at d_re, im at d_im) = A B for the complex operands whose plane groups start at
-// shared addresses a and b (A as rows, B as rows of B^T), four split products per real product.
+// shared addresses a and b (A as rows, B as rows of B^T), four split products per real product, or
+// three (no lo*lo) when LL is false.
+template <bool LL = true>
 __device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t plane, int NP, uint32_t d_re,
                                             uint32_t d_im) {
     const uint32_t lbo = 128, sbo = (uint32_t)(NP >> 3) * 128u;
@@ -127,15 +129,17 @@ __device__ __forceinline__ void issue_cprod(uint32_t a, uint32_t b, uint32_t pla
     // (lo,lo), (hi,lo), (lo,hi) first, (hi,hi) last: the accumulator rounds each addition relative to
     // its running magnitude, so the small terms are summed while it is still small and only the K/16
     // large (hi,hi) additions meet a large accumulator.  Dropping lo*lo would bias products such as
-    // X X, whose lo parts are correlated.
-    const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        const uint64_t ar0 = dA + ha[t] * pl, ai0 = dA + (2 + ha[t]) * pl;
-        const uint64_t br0 = dB + hb[t] * pl, bi0 = dB + (2 + hb[t]) * pl;
+    // X X, whose lo parts are correlated; in a Horner step S Y (unrelated operands) its terms average
+    // out like rounding noise and it is left out.
+    constexpr int t0 = LL ? 0 : 1;
+#pragma unroll 1
+    for (int t = t0; t < 4; ++t) {
+        const int ha = !(t & 1), hb = t < 2;  // lo parts at plane offset 1: (1,1), (0,1), (1,0), (0,0)
+        const uint64_t ar0 = dA + ha * pl, ai0 = dA + (2 + ha) * pl;
+        const uint64_t br0 = dB + hb * pl, bi0 = dB + (2 + hb) * pl;
         for (int kk = 0; kk < NP / 16; ++kk) {
             const uint64_t st = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
-            const int acc = (kk > 0 || t > 0);
+            const int acc = (kk > 0 || t > t0);
             // the two accumulators alternate, so that consecutive MMAs do not chain on one another
             mma_f16(d_re, ar0 + st, br0 + st, pos, acc);
             mma_f16(d_im, ar0 + st, bi0 + st, pos, acc);
@@ -375,6 +379,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                     atomicAdd(P.stats + 0, m3 * (unsigned long long)(bq >= 2 ? bq : 0));
                     atomicAdd(P.stats + 1, m3 * (unsigned long long)bs);
                     atomicAdd(P.stats + 2, 1ull);
+                    if (bq >= 2) atomicAdd(P.stats + 5, m3 * (unsigned long long)(bq - 1));  // Horner: 3 split terms
                 }
             }
             __syncthreads();
@@ -493,7 +498,7 @@ expm_tc_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const i
                 for (int j = q - 2; j >= 0 && !failed; --j) {
                     if (threadIdx.x == 0) {
                         tc_fence_after();
-                        issue_cprod(aA, aBT, plane, NP, T0re, T0im);
+                        issue_cprod<false>(aA, aBT, plane, NP, T0re, T0im);
                         mma_commit(&bar);
                     }
                     if (!mma_wait()) { failed = true; break; }

@@ -410,7 +410,8 @@ __global__ void gg_planes_kernel(DevPlan P, const GgBlock* __restrict__ gb, int 
 
 // Y = H_stack X_p on the tensor cores: one CTA per (128 x 128 output tile, block): rows of the stacked
 // H against columns of X, K in chunks of 32 through a 3-stage ring of bulk copies (A slab + B slab);
-// one thread issues the MMAs two chunks behind the copies; the epilogue writes Y[col][R] in FP32.
+// one thread issues the MMAs two chunks behind the copies (without the (lo, lo) products: H and X are
+// unrelated matrices); the epilogue writes Y[col][R] in FP32.
 __global__ void __launch_bounds__(GT_THREADS, 1)
 gg_tc_kernel(DevPlan P, const GgBlock* __restrict__ gb, const int4* __restrict__ tiles, int p,
              const int* __restrict__ Pmax, const unsigned char* __restrict__ hpl, const unsigned char* __restrict__ xpl,
@@ -468,7 +469,7 @@ gg_tc_kernel(DevPlan P, const GgBlock* __restrict__ gb, const int4* __restrict__
             }
             consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + st * XL_STAGE, ch == 0, false, false, hre, him, cre, cim);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, false, false, false, hre, him, cre, cim);
             mma_commit(&empty[st]);
             if (ch >= 1 && issued < nch) {
                 const int pc = ch - 1;

@@ -1147,7 +1147,7 @@ int qoc_plan_work_counts(qoc_plan* p, long long* out, int n) {
     unsigned long long h[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     cudaError_t e = cudaMemcpy(h, p->d_stats, sizeof(h), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "stats read");
-    for (int i = 0; i < n && i < 5; ++i) out[i] = (long long)h[i];
+    for (int i = 0; i < n && i < 6; ++i) out[i] = (long long)h[i];
     return QOC_OK;
 }
 

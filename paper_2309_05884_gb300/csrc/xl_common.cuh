@@ -6,8 +6,11 @@
 // no-swizzle core layout that the MMA descriptors read, so that one bulk copy moves a slab into
 // shared memory.  A complex product issues 16 kind::f16 MMAs per K step of 16: four real products for
 // each of the four split combinations; the (hi, hi) products accumulate in one pair of TMEM
-// accumulators and the three smaller ones in another, added in FP32 at the end, so the small terms
-// are never rounded against a long running sum.
+// accumulators and the smaller ones in another, added in FP32 at the end, so the small terms are
+// never rounded against a long running sum.  Products whose operands' lo parts are independent may
+// leave out (lo, lo) (12 MMAs): its terms, below 2^-22 of |a||b| each, then average out like rounding
+// noise.  Where they are correlated (X X with X anti-Hermitian: the diagonal sums -|lo|^2), they add
+// up to a bias that a chain of slice propagators turns into a drift of the norm.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -60,27 +63,29 @@ __device__ __forceinline__ bool xl_put8(unsigned char* slab, int off, const floa
     return ok;
 }
 
-// One thread: the MMAs of one staged chunk.  Corrections (lo lo, hi lo, lo hi) into (cre, cim), the
-// (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
+// One thread: the MMAs of one staged chunk.  Corrections (lo lo if ll, hi lo, lo hi) into (cre, cim),
+// the (hi, hi) products into (hre, him); first: the first chunk (overwrite instead of accumulate).
 // nre: the A operand's real planes hold -Re(A); nbre: the B operand's real planes hold -Re(B) (the
 // products that read them are negated).
-__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, bool nbre, uint32_t hre, uint32_t him,
-                                         uint32_t cre, uint32_t cim) {
+__device__ __forceinline__ void xl_issue(uint32_t st, bool first, bool nre, bool nbre, bool ll, uint32_t hre,
+                                         uint32_t him, uint32_t cre, uint32_t cim) {
     const uint32_t lbo = 128, sbo = (XL_KC / 8) * 128;
     const uint32_t pos = idesc_f16(XL_TM, XL_TM, false), neg = idesc_f16(XL_TM, XL_TM, true);
     const uint64_t dA = smem_desc_u32(st, lbo, sbo), dB = smem_desc_u32(st + XL_SLAB, lbo, sbo);
     const uint64_t pl = XL_PLANE >> 4;
     const int ha[4] = {1, 0, 1, 0}, hb[4] = {1, 1, 0, 0};  // (lo,lo), (hi,lo), (lo,hi), (hi,hi)
     const uint32_t s_rr = (nre != nbre) ? neg : pos, s_ri = nre ? neg : pos, s_ir = nbre ? neg : pos;
+    const int t0 = ll ? 0 : 1;
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
+        if (t < t0) continue;
         const uint32_t dre = t < 3 ? cre : hre, dim = t < 3 ? cim : him;
         const uint64_t ar0 = dA + ha[t] * pl, ai0 = dA + (2 + ha[t]) * pl;
         const uint64_t br0 = dB + hb[t] * pl, bi0 = dB + (2 + hb[t]) * pl;
 #pragma unroll
         for (int kk = 0; kk < XL_KC / 16; ++kk) {
             const uint64_t s = (uint64_t)kk * 16u;  // 256 bytes: two core matrices along K
-            const int acc = !(first && kk == 0 && (t == 0 || t == 3));
+            const int acc = !(first && kk == 0 && (t == t0 || t == 3));
             mma_f16(dre, ar0 + s, br0 + s, s_rr, acc);  // Re += Ar Br
             mma_f16(dim, ar0 + s, bi0 + s, s_ri, acc);  // Im += Ar Bi
             mma_f16(dre, ai0 + s, bi0 + s, neg, 1);     // Re -= Ai Bi

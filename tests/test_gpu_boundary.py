@@ -194,6 +194,7 @@ def test_forward_runs_no_derivative_kernel(seg):
     c_fwd = plan.work_counts()
     assert c_fwd[2] > 0          # propagators were computed
     assert c_fwd[3] == 0         # no slice-derivative series ran
+    assert 0 <= c_fwd[5] <= c_fwd[0] + c_fwd[1]  # three-term products are a part of all products
     F = api.FidelityGrad.apply(u, plan, d0, df)
     torch.cuda.synchronize()
     c_mid = plan.work_counts()
