@@ -46,6 +46,11 @@ __constant__ float xl_coef[36] = {
     3.279889237e-30f, 1.130996289e-31f, 3.769987629e-33f, 1.216125042e-34f,
     3.800390755e-36f, 1.151633562e-37f, 3.387157536e-39f, 9.677592959e-41f};
 
+// row stride (entries) of the staged FP32 output tile: 1040 bytes, so that the 16-byte stores of
+// eight consecutive rows cover all 32 banks
+constexpr int XL_UST = XL_TM + 2;
+static_assert((size_t)XL_TM * XL_UST * 8 <= (size_t)XL_STAGES * XL_STAGE, "staged tile fits the copy ring");
+
 // per slice of a chunk
 struct XlItem {
     int bi, kw, k;   // block, window slot, slice (0-based)
@@ -252,10 +257,16 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
     }
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (warp == 0) {
-        tmem_alloc(&tslot, XL_TMEM_COLS);
-        tmem_relinquish();
-    }
+    // chunk ch sits in stage ch % XL_STAGES; its copies complete phase ch / XL_STAGES of full[], its
+    // MMAs the same phase of empty[].  The first copies go out before the tensor memory is allocated.
+    const int nch = (m + XL_KC - 1) / XL_KC;
+    auto load = [&](int ch) {
+        const int st = ch % XL_STAGES;
+        mbar_arrive_expect_tx(&full[st], XL_STAGE);
+        bulk_copy_g2s(sm + st * XL_STAGE, Apl + xl_slab(tm, ch, mp), XL_SLAB, &full[st]);
+        bulk_copy_g2s(sm + st * XL_STAGE + XL_SLAB, Bpl + xl_slab(tn, ch, mp), XL_SLAB, &full[st]);
+    };
+    int issued = 0;
     if (threadIdx.x == 0) {
         for (int i = 0; i < XL_STAGES; ++i) {
             mbar_init(&full[i], 1);
@@ -263,7 +274,18 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
         }
         mbar_init(&done, 1);
         fence_mbar_init();
+        for (; issued < XL_STAGES && issued < nch; ++issued) load(issued);
     }
+    __syncwarp();
+    if (warp == 0) {
+        tmem_alloc(&tslot, XL_TMEM_COLS);
+        tmem_relinquish();
+    }
+    // the epilogue's rows and columns: warp w drains TMEM lanes 32 (w % 4) .. + 31 (tile rows),
+    // columns 32 (w / 4) .. + 31
+    const int quarter = warp & 3, cg = warp >> 2;
+    const int lrow = 32 * quarter + lane, r = row0 + lrow;
+    float2 xv[4][8];
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
@@ -272,18 +294,8 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
     const uint32_t sbase = smem_u32(sm);
 
     if (threadIdx.x == 0) {
-        // chunk ch sits in stage ch % XL_STAGES; its copies complete phase ch / XL_STAGES of full[],
-        // its MMAs the same phase of empty[]
-        const int nch = (m + XL_KC - 1) / XL_KC;
-        auto load = [&](int ch) {
-            const int st = ch % XL_STAGES;
-            mbar_arrive_expect_tx(&full[st], XL_STAGE);
-            bulk_copy_g2s(sm + st * XL_STAGE, Apl + xl_slab(tm, ch, mp), XL_SLAB, &full[st]);
-            bulk_copy_g2s(sm + st * XL_STAGE + XL_SLAB, Bpl + xl_slab(tn, ch, mp), XL_SLAB, &full[st]);
-        };
-        int issued = 0, consumed = 0;
+        int consumed = 0;
         bool fail = false;
-        for (; issued < XL_STAGES && issued < nch; ++issued) load(issued);
         for (int ch = 0; ch < nch; ++ch) {
             const int st = ch % XL_STAGES;
             if (!mbar_wait_bounded(&full[st], (uint32_t)((ch / XL_STAGES) & 1), XL_WAIT_NS)) {
@@ -312,17 +324,29 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
         }
         s_fail = fail;
     }
+    // a Horner step's X entries, fetched while the MMAs run: warps 1.. at once, warp 0 (which holds
+    // the MMA thread, and whose other lanes would hold it up) once every MMA has been issued, while
+    // the last chunks are still in the tensor pipe
+    auto fetch_x = [&]() {
+#pragma unroll
+        for (int g = 0; g < 4; ++g)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const int col = col0 + 32 * cg + 8 * g + c;
+                xv[g][c] = (r < m && col < m) ? __ldg(&M.X[(size_t)r * m + col]) : make_float2(0.f, 0.f);
+            }
+    };
+    if (mode == 1 && warp != 0) fetch_x();
     __syncthreads();
+    if (mode == 1 && warp == 0) fetch_x();
     // every thread waits for the MMAs, also after a failure (the tensor memory is freed below)
     const bool fin = mbar_wait_bounded(&done, 0, XL_WAIT_NS);
     if (!__syncthreads_or(!fin || s_fail)) {
         tc_fence_after();
-        // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31 (tile rows), columns 32 (w / 4) .. + 31
-        const int quarter = warp & 3, cg = warp >> 2;
-        const int lrow = 32 * quarter + lane, r = row0 + lrow;
         const uint32_t lb = (uint32_t)(32 * quarter) << 16;
         float2* Uo = Uout + B.u_off + (size_t)X.kw * B.mmp;
         bool inrange = true;
+#pragma unroll
         for (int g = 0; g < 4; ++g) {
             const int cl = 32 * cg + 8 * g;  // tile column of the group's first entry
             uint32_t a[8], b[8], cc[8], d[8];
@@ -341,7 +365,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
                 for (int c = 0; c < 8; ++c) {
                     const int col = col0 + cl + c;
                     if (col < m) {
-                        const float2 x = M.X[(size_t)r * m + col];
+                        const float2 x = xv[g][c];
                         v[c].x = fmaf(c1, x.x, v[c].x) + (r == col ? c0 : 0.f);
                         v[c].y = fmaf(c1, x.y, v[c].y);
                     }
@@ -350,13 +374,24 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
             if (Opl) {
                 inrange = xl_put8(Opl + xl_slab(tm, (col0 + cl) / XL_KC, mp), xl_off(lrow, cl % XL_KC), v, sout) &&
                           inrange;
-            } else if (r < m) {
+            } else {
+                // U tile staged in the (now idle) copy ring, rows padded to XL_UST entries
+                float2* T = reinterpret_cast<float2*>(sm);
 #pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (col0 + cl + c < m) Uo[(size_t)r * m + col0 + cl + c] = v[c];
+                for (int c = 0; c < 8; c += 2)
+                    *reinterpret_cast<float4*>(&T[lrow * XL_UST + cl + c]) =
+                        make_float4(v[c].x, v[c].y, v[c + 1].x, v[c + 1].y);
             }
         }
         if (!inrange) atomicOr(P.status, ST_RANGE);
+        if (!Opl) {
+            // whole rows of the tile to the propagator store, a warp per row: coalesced
+            __syncthreads();
+            const float2* T = reinterpret_cast<const float2*>(sm);
+            const int ncol = min(XL_TM, m - col0);
+            for (int rr = warp; rr < XL_TM && row0 + rr < m; rr += XL_THREADS / 32)
+                for (int c = lane; c < ncol; c += 32) Uo[(size_t)(row0 + rr) * m + col0 + c] = T[rr * XL_UST + c];
+        }
     } else if (threadIdx.x == 0) {
         atomicOr(P.status, ST_TIMEOUT);
     }
