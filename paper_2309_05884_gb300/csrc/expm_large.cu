@@ -7,8 +7,8 @@
 // chunk of slices in a global scratch area.
 //   xl_prep      per slice: norm bound, Taylor degree, power-of-two operand scales, ownership (slices
 //                that need squarings are left to the CUDA-core tiles);
-//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j) in FP32, and the split operand planes of X and of
-//                S = c_{2q-1} X + c_{2q-2} I;
+//   xl_assemble  X = -i tau (H0 + sum_j u_j Hc_j) in FP32, kept only as the split operand planes of X
+//                (from which the epilogues that add c X read it back) and of S = c_{2q-1} X + c_{2q-2} I;
 //   xl_gemm      Y^T = X^T X^T, then S <- S Y + c_{2j+1} X + c_{2j} I for j = q-2 .. 0; the last step
 //                writes U = T(X) into the propagator store;
 //   xl_export    U = I + X for the slices of degree 1.
@@ -51,6 +51,19 @@ __constant__ float xl_coef[36] = {
 constexpr int XL_UST = XL_TM + 2;
 static_assert((size_t)XL_TM * XL_UST * 8 <= (size_t)XL_STAGES * XL_STAGE, "staged tile fits the copy ring");
 
+// Eight consecutive K entries of one slab row back from their four planes (the inverse of xl_put8 up
+// to the split's 22-bit precision), times inv_s.
+__device__ __forceinline__ void xl_get8(const unsigned char* __restrict__ slab, int off, float inv_s, float2 (&v)[8]) {
+    __half h[4][8];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+        *reinterpret_cast<uint4*>(h[p]) = __ldg(reinterpret_cast<const uint4*>(slab + p * XL_PLANE + off * 2));
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+        v[c] = make_float2((__half2float(h[0][c]) + __half2float(h[1][c])) * inv_s,
+                           (__half2float(h[2][c]) + __half2float(h[3][c])) * inv_s);
+}
+
 // per slice of a chunk
 struct XlItem {
     int bi, kw, k;   // block, window slot, slice (0-based)
@@ -60,16 +73,14 @@ struct XlItem {
     float sc;        // tau (no squarings)
 };
 
-// Scratch of one slice: X in FP32 [m][m] (xbytes), then four plane sets of pbytes each.
+// Scratch of one slice: four plane sets of pbytes each.
 struct XlMats {
-    float2* X;
     unsigned char *XA, *YT, *S0, *S1;  // X (A side), Y (B side) = Y^T (A side), S ping-pong
 };
-__device__ __forceinline__ XlMats xl_mats(unsigned char* scratch, int slice, size_t xbytes, size_t pbytes) {
-    unsigned char* b = scratch + (size_t)slice * (xbytes + 4 * pbytes);
+__device__ __forceinline__ XlMats xl_mats(unsigned char* scratch, int slice, size_t pbytes) {
+    unsigned char* b = scratch + (size_t)slice * (4 * pbytes);
     XlMats M;
-    M.X = reinterpret_cast<float2*>(b);
-    M.XA = b + xbytes;
+    M.XA = b;
     M.YT = M.XA + pbytes;
     M.S0 = M.YT + pbytes;
     M.S1 = M.S0 + pbytes;
@@ -126,8 +137,9 @@ __global__ void xl_prep_kernel(DevPlan P, ExpmTables tabs, const double* __restr
     items[t] = X;
 }
 
-// For every owned slice of the chunk (all of one block): X = -i sc (H0 + sum_j u_j Hc_j) in FP32, the
-// A-side planes of X (scale 2^eX) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I (scale 2^eS, in S1
+// For every owned slice of the chunk (all of one block): X = -i sc (H0 + sum_j u_j Hc_j), formed in
+// FP32 and stored only as the A-side planes of X (scale 2^eX; the Horner epilogues read X back from
+// them) and, for q >= 2, of S = c_{2q-1} X + c_{2q-2} I (scale 2^eS, in S1
 // where the first Horner step reads it), zero outside the m x m block.  A thread owns one group of
 // eight consecutive K entries (r, 8g..8g+7) of one slab row for every slice of the chunk: it reads
 // the block's H0 and Hc_j entries there once and writes them out, combined, slice after slice.  Rows
@@ -135,7 +147,7 @@ __global__ void xl_prep_kernel(DevPlan P, ExpmTables tabs, const double* __restr
 template <int NC>
 __global__ void __launch_bounds__(256, NC <= 3 ? 2 : 1)
 xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __restrict__ items, int n,
-                   unsigned char* __restrict__ scratch, size_t xbytes, size_t pbytes) {
+                   unsigned char* __restrict__ scratch, size_t pbytes) {
     __shared__ float s_u[256][NC];
     __shared__ float s_sc[256], s_sX[256], s_sS[256], s_c1[256], s_c0[256];
     __shared__ int s_q[256];  // 0: not owned; else the Horner count q
@@ -158,7 +170,7 @@ xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __rest
         s_c0[t] = X.q >= 1 ? xl_coef[2 * X.q - 2] : 0.f;
     }
     __syncthreads();
-    const size_t stride = xbytes + 4 * pbytes;  // one slice's scratch
+    const size_t stride = 4 * pbytes;  // one slice's scratch
     const long long G = (long long)mp * ng;
     bool ok = true;
     for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < G;
@@ -173,7 +185,6 @@ xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __rest
                 h[jj][c] = (r < m && k < m) ? H[(size_t)jj * mm + (size_t)r * m + k] : make_float2(0.f, 0.f);
             }
         const size_t pl = xl_slab(r / XL_TM, (8 * g) / XL_KC, mp) + (size_t)xl_off(r % XL_TM, (8 * g) % XL_KC) * 2;
-        const size_t xo = ((size_t)r * m + 8 * g) * sizeof(float2);
         unsigned char* base = scratch;
         for (int t = 0; t < n; ++t, base += stride) {
             const int q = s_q[t];
@@ -190,13 +201,7 @@ xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __rest
                 }
                 v[c] = make_float2(a.y * sc, -a.x * sc);
             }
-            if (r < m) {
-                float2* xr = reinterpret_cast<float2*>(base + xo);
-#pragma unroll
-                for (int c = 0; c < 8; ++c)
-                    if (8 * g + c < m) xr[c] = v[c];
-            }
-            ok = xl_put8(base + xbytes + pl, 0, v, s_sX[t]) && ok;
+            ok = xl_put8(base + pl, 0, v, s_sX[t]) && ok;
             if (q >= 2) {
                 const float c1 = s_c1[t], c0 = s_c0[t];
 #pragma unroll
@@ -204,7 +209,7 @@ xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __rest
                     v[c].x = c1 * v[c].x + (r == 8 * g + c && r < m ? c0 : 0.f);
                     v[c].y = c1 * v[c].y;
                 }
-                ok = xl_put8(base + xbytes + 3 * pbytes + pl, 0, v, s_sS[t]) && ok;
+                ok = xl_put8(base + 3 * pbytes + pl, 0, v, s_sS[t]) && ok;
             }
         }
     }
@@ -220,8 +225,8 @@ xl_assemble_kernel(DevPlan P, const double* __restrict__ u, const XlItem* __rest
 // (the lo parts of X and X^T are correlated); the Horner products, whose operands are different
 // matrices, leave them out.
 __global__ void __launch_bounds__(XL_THREADS, 1)
-xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch, size_t xbytes,
-               size_t pbytes, int tiles_n, int mode, int j, float2* __restrict__ Uout) {
+xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch, size_t pbytes,
+               int tiles_n, int mode, int j, float2* __restrict__ Uout) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t full[XL_STAGES], empty[XL_STAGES], done;
     __shared__ uint32_t tslot;
@@ -235,7 +240,7 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
     const int row0 = tm * XL_TM, col0 = tn * XL_TM;
     if (row0 >= mp || col0 >= mp) return;
 
-    const XlMats M = xl_mats(scratch, blockIdx.y, xbytes, pbytes);
+    const XlMats M = xl_mats(scratch, blockIdx.y, pbytes);
     const unsigned char *Apl, *Bpl;
     unsigned char* Opl = nullptr;
     float unscale, sout = 1.f, c1 = 0.f, c0 = 0.f;
@@ -327,14 +332,13 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
     // a Horner step's X entries, fetched while the MMAs run: warps 1.. at once, warp 0 (which holds
     // the MMA thread, and whose other lanes would hold it up) once every MMA has been issued, while
     // the last chunks are still in the tensor pipe
-    auto fetch_x = [&]() {
+    auto fetch_x = [&]() {  // from the A-side planes of X (zero outside the block)
+        const float inv = ldexpf(1.f, -X.eX);
 #pragma unroll
-        for (int g = 0; g < 4; ++g)
-#pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                const int col = col0 + 32 * cg + 8 * g + c;
-                xv[g][c] = (r < m && col < m) ? __ldg(&M.X[(size_t)r * m + col]) : make_float2(0.f, 0.f);
-            }
+        for (int g = 0; g < 4; ++g) {
+            const int cl = 32 * cg + 8 * g;
+            xl_get8(M.XA + xl_slab(tm, (col0 + cl) / XL_KC, mp), xl_off(lrow, cl % XL_KC), inv, xv[g]);
+        }
     };
     if (mode == 1 && warp != 0) fetch_x();
     __syncthreads();
@@ -401,30 +405,35 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
 }
 
 // U = I + X for every owned slice of degree 1 (the GEMM chain writes U for the others).
+// X is read back from its A-side planes, eight entries of a row per thread.
 __global__ void xl_export_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __restrict__ scratch,
-                                 size_t xbytes, size_t pbytes, float2* __restrict__ Uout) {
+                                 size_t pbytes, float2* __restrict__ Uout) {
     const XlItem& X = items[blockIdx.y];
     if (!X.own || X.q >= 2) return;
     const DevBlock& B = P.blocks[X.bi];
-    const int m = B.m;
-    const size_t mm = (size_t)m * m;
-    const float2* src = xl_mats(scratch, blockIdx.y, xbytes, pbytes).X;
+    const int m = B.m, mp = xl_pad(m), ng = (m + 7) / 8;
+    const unsigned char* XA = xl_mats(scratch, blockIdx.y, pbytes).XA;
+    const float inv = ldexpf(1.f, -X.eX);
     float2* Uo = Uout + B.u_off + (size_t)X.kw * B.mmp;
-    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mm; e += (size_t)gridDim.x * blockDim.x) {
-        float2 v = src[e];
-        const int r = (int)(e / m), c = (int)(e - (size_t)r * m);
-        if (r == c) v.x += 1.f;
-        Uo[e] = v;
+    const long long G = (long long)m * ng;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < G; e += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(e / ng), g = (int)(e - (long long)r * ng);
+        float2 v[8];
+        xl_get8(XA + xl_slab(r / XL_TM, (8 * g) / XL_KC, mp), xl_off(r % XL_TM, (8 * g) % XL_KC), inv, v);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+            const int col = 8 * g + c;
+            if (col < m) Uo[(size_t)r * m + col] = make_float2(v[c].x + (r == col ? 1.f : 0.f), v[c].y);
+        }
     }
 }
 
 }  // namespace
 
 namespace {
-// bytes of one slice's scratch: X in FP32, then four plane sets of the padded size
-size_t xl_xbytes(int m_max) { return ((size_t)m_max * m_max * sizeof(float2) + 1023) / 1024 * 1024; }
+// bytes of one slice's scratch: four plane sets of the padded size
 size_t xl_pbytes(int m_max) { return (size_t)8 * xl_pad(m_max) * xl_pad(m_max); }
-size_t xl_item_bytes(int m_max) { return xl_xbytes(m_max) + 4 * xl_pbytes(m_max); }
+size_t xl_item_bytes(int m_max) { return 4 * xl_pbytes(m_max); }
 
 // slices per chunk: scratch of at most ~2 GiB, at most 256 slices, at least one
 long long xl_chunk(int m_max, long long max_items) {
@@ -464,27 +473,27 @@ int launch_expm_large(const DevPlan& P, const ExpmTables& tabs, const double* u,
     for (int c = 0; c < n_cls; ++c) {
         const int mb = hm[c];
         const long long cnt = hcount[c];
-        const size_t xb = xl_xbytes(mb), pb = xl_pbytes(mb);
+        const size_t pb = xl_pbytes(mb);
         const long long ch = std::max(1LL, std::min<long long>({256LL, cnt, (long long)(budget / xl_item_bytes(mb))}));
         const int tiles = xl_pad(mb) / XL_TM;
         const long long groups = (long long)xl_pad(mb) * (xl_pad(mb) / 8);
         const int as_blocks = (int)std::min<long long>(1024, (groups + 255) / 256);
-        const int ew_blocks = (int)std::min<size_t>(64, ((size_t)mb * mb + 255) / 256);
+        const int ew_blocks = (int)std::min<size_t>(64, ((size_t)mb * (mb + 7) / 8 + 255) / 256);
         for (long long i0 = i0b; i0 < i0b + cnt; i0 += ch) {
             const int n = (int)std::min(ch, i0b + cnt - i0);
             xl_prep_kernel<<<(n + 127) / 128, 128, 0, st>>>(P, tabs, u, cls, items, i0, n, it);
             switch (P.nc) {
-#define XL_AS(K) case K: xl_assemble_kernel<K><<<as_blocks, 256, 0, st>>>(P, u, it, n, mats, xb, pb); break;
+#define XL_AS(K) case K: xl_assemble_kernel<K><<<as_blocks, 256, 0, st>>>(P, u, it, n, mats, pb); break;
                 XL_AS(1) XL_AS(2) XL_AS(3) XL_AS(4) XL_AS(5) XL_AS(6) XL_AS(7) XL_AS(8)
 #undef XL_AS
                 default: return -1;
             }
             if (qmax >= 2) {
-                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 0, 0, U);
+                xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, pb, tiles, 0, 0, U);
                 for (int j = qmax - 2; j >= 0; --j)
-                    xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, xb, pb, tiles, 1, j, U);
+                    xl_gemm_kernel<<<dim3(tiles * tiles, n), XL_THREADS, smem, st>>>(P, it, mats, pb, tiles, 1, j, U);
             }
-            xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, xb, pb, U);
+            xl_export_kernel<<<dim3(ew_blocks, n), 256, 0, st>>>(P, it, mats, pb, U);
             if (cudaGetLastError() != cudaSuccess) return -1;
         }
         i0b += cnt;
