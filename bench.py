@@ -72,8 +72,9 @@ def measured_peaks(long_step: bool = False):
 # algorithmic bytes; None where the kernel changed after the capture.  The profiles/ summaries
 # name the commands.
 NCU_TRAFFIC = {
-    "d14": {"kernel": "xl_gemm_kernel", "bytes": 735.6e6 + 340.1e6, "algorithmic_bytes": 734e6 + 367e6,
-            "launch": "first product of the first chunk: 28 slices of the m = 1179 block, 100 tiles each",
+    "d14": {"kernel": "xl_gemm_kernel", "bytes": 1627.8e6 + 499.9e6, "algorithmic_bytes": 40 * 4 * 13.1072e6,
+            "launch": "Horner step j = 3 of the first chunk: 40 slices of the m = 1179 block, 100 tiles each "
+                      "(reads S, Y^T and X planes, writes S planes: 4 x 13.1 MB per slice)",
             "source": "profiles/xl_gemm_kernel_d14.md"},
 }
 
@@ -325,7 +326,9 @@ class D14:
         return plan, u0, b0, bf
 
     def sweep_bytes(self, plan):
-        return 0  # the checkpointed passes time sweeps together with the exponentials
+        # FP32 complex propagators, read three times: the first pass's forward sweep, and in the costate
+        # pass each segment's forward re-sweep (from its checkpoint) and its backward sweep
+        return 3 * 8 * plan.export_elems()
 
     def cpu_rate(self):
         Ns = 4  # about 15 s of oracle work on 16 host cores
@@ -522,6 +525,19 @@ def run_ours(args, rank, world):
             "achieved": grad_flop / (phase_ms["slice_derivatives"] * 1e-3) / 1e12, "peak": FP32_PEAK_TFLOPS,
             "unit": "TFLOP/s", "peak_source": FP32_PEAK_NOTE, "flops_per_step": grad_flop,
             "note": "series work (c (3P+1) + n_ctrl) m^2 complex multiply-adds per (slice, block) item"}
+    gemm_flop = 8.0 * counts[4] / n
+    if gemm_flop > 0 and "slice_derivatives" not in roofs:
+        tc = args.deriv != "cuda"  # the plans' default derivative GEMM runs on the tensor cores
+        roofs["slice_derivatives"] = {
+            "bound": "tensor" if tc else "alu",
+            "kernel": "gg_tc_kernel (tall GEMMs [H0; Hc_j] X on tcgen05, split FP16)" if tc
+            else "gg_gemm_kernel (tall GEMMs on CUDA cores)",
+            "achieved": gemm_flop / (phase_ms["slice_derivatives"] * 1e-3) / 1e12,
+            "peak": peaks["tensor_tflops"] if tc else FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "peak_source": peaks["tensor_note"] if tc else FP32_PEAK_NOTE, "flops_per_step": gemm_flop,
+            "note": "series work per (slice, block) item: (1 + n_ctrl) m^2 2c (P + 1) complex multiply-adds for the "
+                    "chains, c n_ctrl m (P + 1)(P + 2) / 2 for the contraction; the tensor-core GEMM issues 12 real "
+                    "FP16 products (three split terms) per complex multiply-add, so 1/3 of the peak is its ceiling"}
     sweep_bytes = wl.sweep_bytes(plan)
     if sweep_bytes:
         roofs["sweeps"] = {"bound": "hbm", "kernel": "sweep_cluster_kernel" if plan.sweep_cluster() else "sweep_kernel",
