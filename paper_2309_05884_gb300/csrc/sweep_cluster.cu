@@ -4,16 +4,18 @@
 // A sweep is N dependent matrix-vector products; with one CTA per chain (sweep.cu) a step is bounded
 // by that CTA's fetch of the whole U_k.  Here a cluster of CL CTAs walks one (direction, block) chain:
 // CTA q owns rows [q R, q R + R) of every U_k (R = ceil(m / CL)) and streams them through an
-// STAGES-slot cp.async ring, so each SM moves only R m elements per step, far ahead of use; when R
-// rows do not fit a slot (large blocks) the ring carries sub-blocks of RS rows.
+// STAGES-slot ring of bulk copies (one copy per slot: the rows are contiguous in U_k; an mbarrier per
+// slot), so each SM moves only R m elements per step, far ahead of use; when R rows do not fit a slot
+// (large blocks) the ring carries sub-blocks of RS rows.
 //   forward  psi_k = U_k psi_{k-1}: a CTA computes its rows of psi_k into its exchange buffer; after
 //            the cluster barrier every CTA gathers the whole vector from its peers' buffers (DSMEM);
 //   backward lam_{k-1} = U_k^dagger lam_k: a CTA forms the partial sums over its rows for every
 //            output; after the barrier it adds up its own range over the peers' partials.
 // Exchange buffers alternate between steps, so one cluster barrier per step orders both the writes
 // before the peers' reads and those reads before the buffer is written again two steps later.  The
-// barrier and the cp.async waits are hardware waits: every CTA of a cluster runs the same number of
-// steps, and the cluster launch makes its CTAs co-resident.
+// cluster barrier is a hardware wait: every CTA of a cluster runs the same number of steps, and the
+// cluster launch makes its CTAs co-resident.  The slot waits are bounded; one that runs out latches
+// ST_TIMEOUT and the CTA carries on, so that its cluster still reaches every barrier.
 #include <algorithm>
 
 #include "../../include/qoc.h"
@@ -49,19 +51,25 @@ __device__ __forceinline__ double2 ld_cluster(uint32_t a, double2*) {
     asm volatile("ld.shared::cluster.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "r"(a) : "memory");
     return v;
 }
-__device__ __forceinline__ void cp_async(void* dst, const float2* src) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async(void* dst, const double2* src) {
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+constexpr uint64_t SC_WAIT_NS = 2000000000ull;
+
+// elements of one ring slot: RS rows of max_m, one element of lead-in (a bulk copy starts on a 16-byte
+// boundary, an FP32 row may start 8 bytes past one) and one of round-up, kept even
+template <class T>
+__host__ __device__ __forceinline__ size_t sc_slot(int RS, int max_m) {
+    return ((size_t)RS * max_m + 2 + 1) / 2 * 2;
 }
 
-// Dynamic shared memory: U ring [STAGES][RS][m], x [c][m] (this CTA's input: the whole vector
+// Element span of U that one slot copy moves: the first element e0 rounded down to a 16-byte
+// boundary (lead = e0 - start, 0 or 1 for FP32 complex), n elements rounded up to 16 bytes.  Both
+// ends stay inside the slice's slot of the store: its stride mmp is m^2 rounded up to 4, and a
+// misaligned start implies m odd, so m^2 odd and mmp >= m^2 + 1.
+template <class T>
+__device__ __forceinline__ int sc_lead(long long e0) {
+    return sizeof(cx<T>) == 16 ? 0 : (int)(e0 & 1);
+}
+
+// Dynamic shared memory: U ring [STAGES][sc_slot], x [c][m] (this CTA's input: the whole vector
 // forward, its own rows backward), exchange buffers xb[2][c][m].  SUB = false: a slot holds all of a
 // CTA's rows (RS >= R); SUB = true: the rows of a step pass through the ring in sub-blocks of RS.
 template <class T, int STAGES, bool SUB>
@@ -72,6 +80,7 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
                      int RS) {
     extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ cx<T> red[SC_THREADS / 32];
+    __shared__ __align__(8) uint64_t full[STAGES];  // slot s filled: one arrival (the issuing thread) + bytes
     const int chain = (int)(blockIdx.x / (unsigned)CL);
     const int q = (int)cluster_rank();
     const int nfw = (dirs & 1) ? P.nb : 0;
@@ -82,13 +91,35 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
     const long long mmp = B.mmp;
     const int R = (m + CL - 1) / CL;
     const int r0 = min(m, q * R), r1 = min(m, r0 + R), nr = r1 - r0;  // nr may be 0
-    cx<T>* ust = reinterpret_cast<cx<T>*>(dsm);                  // [STAGES][RS * max_m]
-    cx<T>* x = ust + (size_t)STAGES * RS * max_m;                 // [max_c][max_m]
+    const size_t SLOT = sc_slot<T>(RS, max_m);
+    cx<T>* ust = reinterpret_cast<cx<T>*>(dsm);                  // [STAGES][SLOT]
+    cx<T>* x = ust + (size_t)STAGES * SLOT;                       // [max_c][max_m]
     cx<T>* xb = x + (size_t)max_c * max_m;                        // [2][max_c][max_m]
     const size_t xbs = (size_t)max_c * max_m;
     const int tid = threadIdx.x;
     cx<T>* st = fwd ? psi_st : lam_st;
     const long long s0 = B.s_off;
+    if (tid == 0) {
+        for (int s = 0; s < STAGES; ++s) mbar_init(&full[s], 1);
+        fence_mbar_init();
+    }
+    // one bulk copy of n elements of U starting at element e0 into slot s (thread 0; the slot's
+    // previous contents were read before the barrier that precedes this call)
+    auto fill = [&](int s, long long e0, long long n) {
+        if (tid == 0) {
+            const int lead = sc_lead<T>(e0);
+            const long long cnt = sizeof(cx<T>) == 16 ? n : (n + lead + 1) / 2 * 2;  // whole 16-byte units
+            const uint32_t bytes = (uint32_t)(cnt * sizeof(cx<T>));
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive_expect_tx(&full[s], bytes);
+            bulk_copy_g2s(ust + (size_t)s * SLOT, U + (e0 - lead), bytes, &full[s]);
+        }
+    };
+    // wait for fill number f (slot f % STAGES, phase f / STAGES)
+    auto wait_fill = [&](long long f) {
+        if (!mbar_wait_bounded(&full[f % STAGES], (uint32_t)((f / STAGES) & 1), SC_WAIT_NS) && tid == 0)
+            atomicOr(P.status, ST_TIMEOUT);
+    };
 
     // initial vector: forward needs all of it, backward its own rows; slot 0 (fwd) / NK (bwd) holds it
     {
@@ -230,64 +261,58 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
         __syncthreads();
     };
 
+    // first element of step t's rows ra.. of this CTA in U
+    auto first = [&](int t, int ra) {
+        const int i = fwd ? t : NK - 1 - t;
+        return B.u_off + (long long)i * mmp + (long long)(r0 + ra) * m;
+    };
     if constexpr (!SUB) {
         // all of a step's rows in one ring slot, issued STAGES - 1 steps ahead of use
         auto issue = [&](int t) {
-            if (t < NK && nr > 0) {
-                const int i = fwd ? t : NK - 1 - t;
-                const cx<T>* src = U + B.u_off + (long long)i * mmp + (long long)r0 * m;
-                cx<T>* dst = ust + (size_t)(t % STAGES) * RS * max_m;
-                for (int e = tid; e < nr * m; e += SC_THREADS) cp_async(dst + e, src + e);
-            }
-            cp_commit();
+            if (t < NK && nr > 0) fill(t % STAGES, first(t, 0), (long long)nr * m);
         };
         for (int t = 0; t < STAGES - 1; ++t) issue(t);
         __syncthreads();
         const int lg = split(fwd ? nr * c : m * c);
         for (int t = 0; t < NK; ++t) {
             issue(t + STAGES - 1);
-            cp_wait<STAGES - 1>();
-            __syncthreads();
+            if (nr > 0) wait_fill(t);
             cx<T>* out = xb + (size_t)(t & 1) * xbs;
-            compute(ust + (size_t)(t % STAGES) * RS * max_m, 0, nr, lg, true, out);
+            compute(ust + (size_t)(t % STAGES) * SLOT + (nr > 0 ? sc_lead<T>(first(t, 0)) : 0), 0, nr, lg, true, out);
             exchange(t, out);
         }
     } else {
         // sub-blocks of RS rows, issued STAGES - 1 sub-blocks ahead of use
         const int nsb = nr > 0 ? (nr + RS - 1) / RS : 0;
-        int it = 0, isb = 0, islot = 0;  // next sub-block to issue: step, index, ring slot
+        int it = 0, isb = 0;  // next sub-block to issue: step, index
+        long long nfill = 0;  // fills issued (fill f goes to slot f % STAGES)
         auto issue = [&]() {
             if (nsb > 0 && it < NK) {
-                const int i = fwd ? it : NK - 1 - it;
                 const int ra = isb * RS, rn = min(RS, nr - ra);
-                const cx<T>* src = U + B.u_off + (long long)i * mmp + (long long)(r0 + ra) * m;
-                cx<T>* dst = ust + (size_t)islot * RS * max_m;
-                for (int e = tid; e < rn * m; e += SC_THREADS) cp_async(dst + e, src + e);
+                fill((int)(nfill % STAGES), first(it, ra), (long long)rn * m);
+                ++nfill;
                 if (++isb == nsb) {
                     isb = 0;
                     ++it;
                 }
-                if (++islot == STAGES) islot = 0;
             }
-            cp_commit();
         };
         for (int g = 0; g < STAGES - 1; ++g) issue();
         __syncthreads();
         const int rn_last = nr - (nsb - 1) * RS;
         const int lg_full = split(fwd ? RS * c : m * c), lg_last = split(fwd ? rn_last * c : m * c);
-        int cslot = 0;  // ring slot of the sub-block in use
+        long long cfill = 0;  // the fill in use
         for (int t = 0; t < NK; ++t) {
             cx<T>* out = xb + (size_t)(t & 1) * xbs;
             if (!fwd && nsb == 0)  // no rows: this CTA's partial sums are zero
                 for (int e = tid; e < m * c; e += SC_THREADS) out[(size_t)(e / m) * max_m + e % m] = mk<T>(0, 0);
             for (int sb = 0; sb < nsb; ++sb) {
                 issue();
-                cp_wait<STAGES - 1>();
-                __syncthreads();
+                wait_fill(cfill);
                 const bool last = sb + 1 == nsb;
-                compute(ust + (size_t)cslot * RS * max_m, sb * RS, last ? rn_last : RS, last ? lg_last : lg_full,
-                        sb == 0, out);
-                if (++cslot == STAGES) cslot = 0;
+                compute(ust + (size_t)(cfill % STAGES) * SLOT + sc_lead<T>(first(t, sb * RS)), sb * RS,
+                        last ? rn_last : RS, last ? lg_last : lg_full, sb == 0, out);
+                ++cfill;
                 // the slot is refilled and out is extended by the next sub-block (after the last one of
                 // the step the cluster barrier orders both)
                 if (!last) __syncthreads();
@@ -295,7 +320,6 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
             exchange(t, out);
         }
     }
-    cp_wait<0>();
     // final vector (own range) to the boundary output
     cx<T>* fin = (fwd ? fwd_out : bwd_out) + B.v_off;
     for (int e = tid; e < nr * c; e += SC_THREADS) {
@@ -307,7 +331,7 @@ sweep_cluster_kernel(DevPlan P, const cx<T>* __restrict__ U, const cx<T>* __rest
 
 template <class T, int STAGES>
 size_t sc_smem(int max_m, int max_c, int RS) {
-    return ((size_t)STAGES * RS * max_m + 3 * (size_t)max_c * max_m) * sizeof(cx<T>);
+    return ((size_t)STAGES * sc_slot<T>(RS, max_m) + 3 * (size_t)max_c * max_m) * sizeof(cx<T>);
 }
 
 constexpr size_t SC_SMEM_LIMIT = 220 * 1024;
@@ -316,7 +340,7 @@ constexpr size_t SC_SMEM_LIMIT = 220 * 1024;
 template <class T, int STAGES>
 int sc_rows_per_slot(int max_m, int max_c, int CL) {
     const int Rmax = (max_m + CL - 1) / CL;
-    const size_t fixed = 3 * (size_t)max_c * max_m * sizeof(cx<T>);
+    const size_t fixed = (3 * (size_t)max_c * max_m + (size_t)STAGES * 3) * sizeof(cx<T>);  // + slot slack
     if (fixed >= SC_SMEM_LIMIT) return 0;
     const size_t per_row = (size_t)STAGES * max_m * sizeof(cx<T>);
     const long long rs = (long long)((SC_SMEM_LIMIT - fixed) / per_row);
