@@ -19,6 +19,7 @@
 #include <cmath>
 #include <cstring>
 #include <functional>
+#include <limits>
 #include <map>
 #include <new>
 #include <stdexcept>
@@ -88,12 +89,40 @@ void apply_terms(const std::vector<qoc_term>& terms, int n, uint64_t x,
     }
 }
 
-double norm1_max_col(const std::vector<cplx>& M, int m) {
-    double best = 0.0;
-    for (int j = 0; j < m; ++j) {
-        double s = 0.0;
-        for (int i = 0; i < m; ++i) s += std::abs(M[(size_t)i * m + j]);
-        best = std::max(best, s);
+// An upper bound of the spectral norm of a Hermitian block M (m x m, row-major): for the entrywise
+// moduli P = |M|, ||M||_2 = rho(M) <= rho(P) <= max_i (P x)_i / x_i for every positive x
+// (Collatz-Wielandt).  Evaluated along power iterations on P from x = 1 (the first bound is the
+// max row sum, i.e. the 1-norm of a Hermitian matrix), kept positive by a small shift; the smallest
+// bound met is returned.  P is scanned once into its nonzeros, so an iteration costs their number.
+double spectral_bound(const std::vector<cplx>& M, int m) {
+    std::vector<int> ptr(m + 1, 0), col;
+    std::vector<double> val;
+    for (int i = 0; i < m; ++i) {
+        for (int j = 0; j < m; ++j) {
+            const double a = std::abs(M[(size_t)i * m + j]);
+            if (a > 0.0) {
+                col.push_back(j);
+                val.push_back(a);
+            }
+        }
+        ptr[i + 1] = (int)col.size();
+    }
+    if (col.empty()) return 0.0;
+    std::vector<double> x(m, 1.0), y(m);
+    double best = std::numeric_limits<double>::infinity();
+    for (int it = 0; it < 300; ++it) {
+        double hi = 0.0, lo = std::numeric_limits<double>::infinity(), ymax = 0.0;
+        for (int i = 0; i < m; ++i) {
+            double s = 0.0;
+            for (int k = ptr[i]; k < ptr[i + 1]; ++k) s += val[k] * x[col[k]];
+            y[i] = s;
+            hi = std::max(hi, s / x[i]);
+            lo = std::min(lo, s / x[i]);
+            ymax = std::max(ymax, s);
+        }
+        best = std::min(best, hi);
+        if (hi - lo <= 1e-4 * hi || ymax <= 0.0) break;
+        for (int i = 0; i < m; ++i) x[i] = y[i] / ymax + 1e-6;
     }
     return best;
 }
@@ -237,10 +266,10 @@ void build_sn(qoc_basis& B, const std::vector<qoc_term>& h0,
         blk.c = (int)std::min<uint64_t>(copies, 1ULL << 30);
         blk.label = (J2 % 2 == 0) ? ("J=" + std::to_string(J2 / 2)) : ("J=" + std::to_string(J2) + "/2");
         blk.h0 = block_of(h0, J2);
-        blk.h0_norm1 = norm1_max_col(blk.h0, blk.m);
+        blk.h0_norm = spectral_bound(blk.h0, blk.m);
         for (auto& l : hc) {
             auto M = block_of(l, J2);
-            blk.hc_norm1.push_back(norm1_max_col(M, blk.m));
+            blk.hc_norm.push_back(spectral_bound(M, blk.m));
             blk.hc.insert(blk.hc.end(), M.begin(), M.end());
         }
         if (vectors) {
@@ -416,10 +445,10 @@ void build_dn(qoc_basis& B, const std::vector<qoc_term>& h0,
             return M;
         };
         blk.h0 = block_of(h0);
-        blk.h0_norm1 = norm1_max_col(blk.h0, m);
+        blk.h0_norm = spectral_bound(blk.h0, m);
         for (auto& l : hc) {
             auto M = block_of(l);
-            blk.hc_norm1.push_back(norm1_max_col(M, m));
+            blk.hc_norm.push_back(spectral_bound(M, m));
             blk.hc.insert(blk.hc.end(), M.begin(), M.end());
         }
         if (want_vectors) {

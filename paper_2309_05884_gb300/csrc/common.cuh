@@ -63,8 +63,8 @@ struct DevBlock {
     int64_t u_off;    // complex offset of U_b[slot 0] in the propagator area (slot i at u_off + i*mmp)
     int64_t s_off;    // complex offset of psi_b[slot 0] in the window state areas (slot i at s_off + i*c*m)
     int64_t v_off;    // complex offset of block b in a boundary-vector array [b][copy][m]
-    double h0_norm1;  // max column 1-norm of H0_b
-    double hc_norm1[8];
+    double h0_norm;  // upper bound of the spectral norm of H0_b (hc_norm: of each Hc_jb)
+    double hc_norm[8];
 };
 
 // GRAPE update rule applied by the reduction kernel (after F and dF/du of an iteration).
@@ -106,15 +106,15 @@ struct DevPlan {
     unsigned long long* stats; // work counters or null
 };
 
-// Norm bound of slice k (0-based) of block B: beta = tau (|H0|_1 + sum_j |u_kj| |Hc_j|_1), the 1-norm
-// bound that fixes the squarings of the exponential and the series lengths (Sec. II.A).  Non-finite
+// Norm bound of slice k (0-based) of block B: beta = tau (|H0|_2 + sum_j |u_kj| |Hc_j|_2) with the
+// per-block bounds of the spectral norms, an upper bound of |A_k|_2 (triangle inequality) that fixes the squarings of the exponential and the series lengths (Sec. II.A).  Non-finite
 // pulse values count as 0 (the kernels latch ST_NAN_PULSE).  Every kernel that decides which
 // slices it owns uses this function, so that the decisions of different kernels agree exactly.
 __device__ __forceinline__ double slice_beta(const DevPlan& P, const DevBlock& B, const double* u, long long k) {
-    double beta = B.h0_norm1;
+    double beta = B.h0_norm;
     for (int j = 0; j < P.nc; ++j) {
         const double x = u[(size_t)(B.u_row + k) * P.nc + j];
-        beta += fabs(isfinite(x) ? x : 0.0) * B.hc_norm1[j];
+        beta += fabs(isfinite(x) ? x : 0.0) * B.hc_norm[j];
     }
     return beta * B.dt;
 }

@@ -2,7 +2,7 @@
 //
 // Scaling and squaring with a truncated Taylor polynomial of degree d evaluated by the
 // Paterson-Stockmeyer scheme (d = p*q: p-1 products for X^2..X^p, then q-1 Horner products in
-// X^p).  Per slice and block the 1-norm bound beta = tau (|H0_b|_1 + sum_j |u_kj| |Hc_jb|_1) picks
+// X^p).  Per slice and block the norm bound beta = tau (|H0_b|_2 + sum_j |u_kj| |Hc_jb|_2) picks
 // the number of squarings s and the smallest degree whose truncation bound
 // beta_s^{d+1}/(d+1)! / (1 - beta_s/(d+2)) stays below the working unit roundoff, beta_s = beta/2^s.
 // The polynomial runs in the working precision T (FP32 or FP64); the squaring chain always runs in

@@ -4,7 +4,7 @@
 //
 // Scaling and squaring with a truncated Taylor polynomial of degree d evaluated by the
 // Paterson-Stockmeyer scheme (d = p*q: p-1 products for X^2..X^p, then q-1 Horner products in
-// X^p).  The 1-norm bound beta = tau (|H0_b|_1 + sum_j |u_kj| |Hc_jb|_1) picks the number of
+// X^p).  The norm bound beta = tau (|H0_b|_2 + sum_j |u_kj| |Hc_jb|_2) picks the number of
 // squarings s and the smallest degree whose truncation bound beta_s^{d+1}/(d+1)! / (1 - beta_s/(d+2))
 // stays below the working unit roundoff, beta_s = beta/2^s.  The polynomial runs in the working
 // precision T (FP32 or FP64); the squaring chain runs in FP64 (or in T when tabs.sq_f64 is 0).  The
@@ -58,14 +58,14 @@ __device__ void expm_item(const DevPlan& P, const ExpmTables& tabs, const double
     const size_t mm = (size_t)m * m;
 
     if (threadIdx.x == 0) {
-        double beta = B.h0_norm1;
+        double beta = B.h0_norm;
         int bad = 0;
         for (int j = 0; j < P.nc; ++j) {
             const double uk = u[(size_t)(B.u_row + k) * P.nc + j];
             const int fin = isfinite(uk);
             bad |= !fin;
             sh.s_uk[j] = fin ? uk : 0.0;
-            beta += fabs(sh.s_uk[j]) * B.hc_norm1[j];
+            beta += fabs(sh.s_uk[j]) * B.hc_norm[j];
         }
         if (bad) atomicOr(P.status, ST_NAN_PULSE);
         beta *= B.dt;

@@ -10,7 +10,7 @@
 //     T(X) = sum_{j<q} (c_{2j} I + c_{2j+1} X) Y^j,   c_k = 1/k!,
 // so each step S <- S Y + c_{2j+1} X + c_{2j} I needs only X beside the accumulator, and X stays in
 // tensor memory for the whole item: q products for degree 2q-1 (Y, then q-1 Horner steps).  Per
-// slice, the norm bound beta = tau (|H0|_1 + sum_j |u_j| |Hc_j|_1) fixes the fewest squarings s that
+// slice, the norm bound beta = tau (|H0|_2 + sum_j |u_j| |Hc_j|_2) fixes the fewest squarings s that
 // bring it under the plan's largest norm, then the lowest odd degree whose truncation bound covers
 // beta / 2^s.  With an FP64 squaring chain the squarings run on the CUDA cores.
 //

@@ -89,13 +89,13 @@ expm_warp_kernel(DevPlan P, ExpmTables tabs, const double* __restrict__ u, const
 #pragma unroll
         for (int j = 0; j < 8; ++j) uk[j] = 0.0;
         if (valid) {
-            beta = B.h0_norm1;
+            beta = B.h0_norm;
             for (int j = 0; j < P.nc; ++j) {
                 const double x = u[(size_t)(B.u_row + k) * P.nc + j];
                 const bool fin = isfinite(x);
                 if (!fin && row == 0) atomicOr(P.status, ST_NAN_PULSE);
                 uk[j] = fin ? x : 0.0;
-                beta += fabs(uk[j]) * B.hc_norm1[j];
+                beta += fabs(uk[j]) * B.hc_norm[j];
             }
             beta *= B.dt;
         }

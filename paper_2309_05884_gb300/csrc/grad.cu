@@ -4,7 +4,7 @@
 // psi = psi_{k-1} and lam = lam_k (costate), the Frechet derivative of exp gives
 //     lam^dagger L(A, E_j) psi = sum_{p+q<=P} (A^dagger^p lam)^dagger E_j (A^q psi) / (p+q+1)!
 // (the series L(A,E) = sum_{p,q} A^p E A^q / (p+q+1)!, truncated once beta^{P+1}/(P+1)! is below
-// the tolerance, beta the slice's 1-norm bound).  With v_q = A^q psi, w_p = (A^dagger)^p lam = (-A)^p
+// the tolerance, beta the slice's norm bound).  With v_q = A^q psi, w_p = (A^dagger)^p lam = (-A)^p
 // lam and z_q = sum_{p<=P-q} w_p / (p+q+1)!, the sum is
 //     -i tau sum_{a,b} Hc_j[a][b] * M[a][b],   M[a][b] = sum_q conj(z_q[a]) v_q[b],
 // so every Hc_jb is read once per slice.  The paper's own slice derivative (Eq.
@@ -148,11 +148,11 @@ grad_kernel(DevPlan P, double tol, double theta, const double* __restrict__ u, c
             const size_t mm = (size_t)m * m;
             const T tau = (T)B.dt;
             if (threadIdx.x == 0) {
-                double beta = B.h0_norm1;
+                double beta = B.h0_norm;
                 for (int j = 0; j < nc; ++j) {
                     const double uk = u[(size_t)(B.u_row + k - 1) * nc + j];
                     s_uk[j] = isfinite(uk) ? uk : 0.0;
-                    beta += fabs(s_uk[j]) * B.hc_norm1[j];
+                    beta += fabs(s_uk[j]) * B.hc_norm[j];
                 }
                 beta *= B.dt;
                 int Pt = 0, sub = 0;

@@ -6,7 +6,7 @@
 // and A^dagger = -A (H Hermitian), the slice derivative is
 //     lam^dagger L(A_k, E_j) psi = -i tau sum_{a+b <= P} (-1)^a / (a+b+1)! * z_a^dagger (Hc_j v_b),
 //     v_b = A_k^b psi,  z_a = A_k^a lam,
-// truncated once beta^{P+1}/(P+1)! is below the FP32 tolerance (beta the slice's 1-norm bound).
+// truncated once beta^{P+1}/(P+1)! is below the FP32 tolerance (beta the slice's norm bound).
 // Every chain step needs A_k x = -i tau (H0 x + sum_j u_kj Hc_j x), and H0, Hc_j do not depend on
 // the slice: one step for every vector of every slice of the chunk is the product
 //     Y = [H0; Hc_1; ...; Hc_nc] X,   X = [v_p and z_p of every (slice, copy)] (m x 2 c S),

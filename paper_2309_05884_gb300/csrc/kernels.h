@@ -8,7 +8,7 @@
 
 namespace qoc {
 
-// Degree table of the Taylor / Paterson-Stockmeyer scheme: theta[i] is the largest 1-norm bound
+// Degree table of the Taylor / Paterson-Stockmeyer scheme: theta[i] is the largest norm bound
 // for which degree (p_i q_i) keeps the truncation below the working unit roundoff.
 // FP32 exact-derivative series: terms below 2^-27 (about an eighth of the FP32 unit roundoff,
 // relative to the leading term) are dropped

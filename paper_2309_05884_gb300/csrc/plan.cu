@@ -858,8 +858,8 @@ int qoc_plan_create_batch(const qoc_basis* const* bases, int n_problems, const i
         d.u_off = u_off;
         d.s_off = s_off;
         d.v_off = v_off;
-        d.h0_norm1 = blk.h0_norm1;
-        for (int j = 0; j < nc; ++j) d.hc_norm1[j] = blk.hc_norm1[j];
+        d.h0_norm = blk.h0_norm;
+        for (int j = 0; j < nc; ++j) d.hc_norm[j] = blk.hc_norm[j];
         p->copy_base.push_back((int64_t)p->copy_src.size());
         int64_t boff = blk.offset;
         if (gate) {  // block-state layout of the gate objective: [block][column][m]

@@ -26,8 +26,8 @@ struct Block {
     std::string label;
     std::vector<cplx> h0;      // m*m row-major
     std::vector<cplx> hc;      // n_ctrl*m*m
-    double h0_norm1 = 0.0;     // max column 1-norm of H0_b
-    std::vector<double> hc_norm1;
+    double h0_norm = 0.0;     // upper bound of the spectral norm of H0_b (basis.cpp: spectral_bound)
+    std::vector<double> hc_norm;
     std::vector<SparseVec> vecs;  // c*m basis vectors (copy-major), empty without vectors
 };
 

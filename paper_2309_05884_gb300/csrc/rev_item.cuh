@@ -1,7 +1,7 @@
 // One (slice, block) item of the slice derivatives by reverse-mode differentiation of the scaling-and-squaring
 // propagator (Appendix B's slice derivative, exact for the computed U_k).
 //
-// For a slice whose 1-norm bound needs s >= 3 halvings the series of grad.cu would run 2^s
+// For a slice whose norm bound needs s >= 3 halvings the series of grad.cu would run 2^s
 // sub-slices; here the propagator's own computation is differentiated instead.  With X = A/2^s the
 // forward pass recomputes and keeps every intermediate
 //     P_1 = X, P_l = P_{l-1} X (l <= p);  S_{q-1} = c_d P_p + sum_{l<p} c_{(q-1)p+l} P_l + c_{(q-1)p} I,
@@ -70,11 +70,11 @@ __device__ void rev_item(const DevPlan& P, const ExpmTables& tabs, const double*
     const int m = B.m, c = B.c;
     const size_t mm = (size_t)m * m;
     if (threadIdx.x == 0) {
-        double beta = B.h0_norm1;
+        double beta = B.h0_norm;
         for (int j = 0; j < nc; ++j) {
             const double x = u[(size_t)(B.u_row + k - 1) * nc + j];
             sh.s_uk[j] = isfinite(x) ? x : 0.0;
-            beta += fabs(sh.s_uk[j]) * B.hc_norm1[j];
+            beta += fabs(sh.s_uk[j]) * B.hc_norm[j];
         }
         beta *= B.dt;
         int s = 0;
