@@ -72,9 +72,9 @@ def measured_peaks(long_step: bool = False):
 # algorithmic bytes; None where the kernel changed after the capture.  The profiles/ summaries
 # name the commands.
 NCU_TRAFFIC = {
-    "d14": {"kernel": "xl_gemm_kernel", "bytes": 1627.8e6 + 499.9e6, "algorithmic_bytes": 40 * 4 * 13.1072e6,
-            "launch": "Horner step j = 3 of the first chunk: 40 slices of the m = 1179 block, 100 tiles each "
-                      "(reads S, Y^T and X planes, writes S planes: 4 x 13.1 MB per slice)",
+    "d14": {"kernel": "xl_gemm_kernel", "bytes": 933.9e6 + 339.9e6, "algorithmic_bytes": 23 * (3 * 13.1072e6 + 11.1206e6),
+            "launch": "final product U = A(Y) + X B(Y) of the first chunk: 23 slices of the m = 1179 block, 100 tiles "
+                      "each (reads the X, B(Y) and A(Y) planes, 3 x 13.1 MB per slice; writes U, 11.1 MB)",
             "source": "profiles/xl_gemm_kernel_d14.md"},
 }
 
@@ -339,7 +339,7 @@ class D14:
 
 
 WS_T = 4.0
-WS_TRAIN, WS_HELD = 8192, 1024
+WS_TRAIN, WS_HELD = 20000, 1024
 
 
 def run_warmstart(args, rank, world):

@@ -469,7 +469,7 @@ gg_tc_kernel(DevPlan P, const GgBlock* __restrict__ gb, const int4* __restrict__
             }
             consumed = ch + 1;
             tc_fence_after();
-            xl_issue(sbase + st * XL_STAGE, ch == 0, false, false, false, hre, him, cre, cim);
+            xl_issue(sbase + st * XL_STAGE, ch == 0, false, false, false, false, hre, him, cre, cim);
             mma_commit(&empty[st]);
             if (ch >= 1 && issued < nch) {
                 const int pc = ch - 1;

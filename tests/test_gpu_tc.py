@@ -177,13 +177,15 @@ def test_tensor_core_expm_in_checkpoint_windows():
     assert np.abs(res[0][1] - res[1][1]).max() <= 1e-12 * max(1.0, np.abs(res[0][1]).max())
 
 
-def test_large_block_tensor_core_propagators_match_oracle():
-    # D_12 blocks of 128..346 states (two or three 128-row tiles, ragged tails), tau = 0.02: the tiled
+@pytest.mark.parametrize("T", [0.12, 0.003, 0.6])
+def test_large_block_tensor_core_propagators_match_oracle(T):
+    # D_12 blocks of 128..346 states (one to three 128-row tiles, ragged tails), 6 slices of tau = T / 6
+    # (0.02: Taylor degree 9-11; 0.0005: degree 3, no Y^2; 0.1: degree 13-15 or squarings): the tiled
     # tensor-core GEMMs (rule kind 3) against the FP64 oracle and the CUDA-core tiles
     from oracle import grape as gr
     from paper_2309_05884_gb300 import api
     from paper_2309_05884_gb300 import inputs as I
-    s = I.xxz_ring(12, 0.12, 6)
+    s = I.xxz_ring(12, T, 6)
     B = api.Basis(s)
     u = I.pulses_normal(29, s.N, 3)
     plan = api.Plan(B, s.N, s.tau, prec="f32")
