@@ -118,6 +118,13 @@ int qoc_basis_block(const qoc_basis* basis, int b, int* size, int* copies, int64
  * pointer may be NULL. */
 int qoc_basis_block_matrices(const qoc_basis* basis, int b, double* h0, double* hc);
 
+/* Upper bounds of the spectral norms of block b's H0_b (out[0]) and Hc_jb (out[1 + j]), host,
+ * 1 + n_ctrl doubles.  The slice norm bound tau (|H0_b| + sum_j |u_kj| |Hc_jb|) built from them fixes
+ * the Taylor degree, the squarings and the derivative-series lengths (Sec. II.A; the paper states
+ * the truncated series, not the norm).  Each is the Collatz-Wielandt value max_i (|M| x)_i / x_i of
+ * the entrywise moduli along power iterations from x = 1: never below ||M||_2, never above the 1-norm. */
+int qoc_basis_norm_bounds(const qoc_basis* basis, int b, double* out);
+
 /* full (host, 2^n complex) -> blk (host, state_len complex): coordinates <v_{b,r,a}|psi>.
  * Needs the basis vectors (D_n n <= 16, S_n n <= 12, built without QOC_BASIS_NO_VECTORS). */
 int qoc_state_to_blocks(const qoc_basis* basis, const double* full, double* blk);

@@ -62,6 +62,7 @@ SIGNATURES = {
     "qoc_basis_block": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int64),
                                   C.c_char_p]),
     "qoc_basis_block_matrices": (C.c_int, [P, C.c_int, P, P]),
+    "qoc_basis_norm_bounds": (C.c_int, [P, C.c_int, P]),
     "qoc_state_to_blocks": (C.c_int, [P, P, P]),
     "qoc_blocks_to_state": (C.c_int, [P, P, P]),
     "qoc_dicke_state": (C.c_int, [P, C.c_int, P]),

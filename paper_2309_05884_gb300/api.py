@@ -71,6 +71,13 @@ class Basis:
                                                   hc.ctypes.data_as(C.c_void_p)), "qoc_basis_block_matrices")
         return h0, hc
 
+    def norm_bounds(self, b: int) -> np.ndarray:
+        """[bound of |H0_b|_2, bound of |Hc_jb|_2 for each j]: what the slice norm bound is built from."""
+        out = np.zeros(1 + self.n_ctrl, np.float64)
+        L.check(self.lib.qoc_basis_norm_bounds(self.handle, b, out.ctypes.data_as(C.c_void_p)),
+                "qoc_basis_norm_bounds")
+        return out
+
     def state_to_blocks(self, full: np.ndarray) -> np.ndarray:
         full = np.ascontiguousarray(full, dtype=np.complex128)
         assert full.shape == (self.full_dim,)

@@ -91,9 +91,11 @@ void apply_terms(const std::vector<qoc_term>& terms, int n, uint64_t x,
 
 // An upper bound of the spectral norm of a Hermitian block M (m x m, row-major): for the entrywise
 // moduli P = |M|, ||M||_2 = rho(M) <= rho(P) <= max_i (P x)_i / x_i for every positive x
-// (Collatz-Wielandt).  Evaluated along power iterations on P from x = 1 (the first bound is the
-// max row sum, i.e. the 1-norm of a Hermitian matrix), kept positive by a small shift; the smallest
-// bound met is returned.  P is scanned once into its nonzeros, so an iteration costs their number.
+// (Collatz-Wielandt).  Evaluated along power iterations on P + s I from x = 1 (the first bound is the
+// max row sum, i.e. the 1-norm of a Hermitian matrix; the shift s, half of it, keeps the iteration
+// from oscillating when P is bipartite, e.g. a hopping term, and leaves the ratios of P as they are),
+// kept positive by a small floor; the smallest bound met is returned.  P is scanned once into its
+// nonzeros, so an iteration costs their number.
 double spectral_bound(const std::vector<cplx>& M, int m) {
     std::vector<int> ptr(m + 1, 0), col;
     std::vector<double> val;
@@ -109,7 +111,7 @@ double spectral_bound(const std::vector<cplx>& M, int m) {
     }
     if (col.empty()) return 0.0;
     std::vector<double> x(m, 1.0), y(m);
-    double best = std::numeric_limits<double>::infinity();
+    double best = std::numeric_limits<double>::infinity(), shift = -1.0;
     for (int it = 0; it < 300; ++it) {
         double hi = 0.0, lo = std::numeric_limits<double>::infinity(), ymax = 0.0;
         for (int i = 0; i < m; ++i) {
@@ -122,7 +124,13 @@ double spectral_bound(const std::vector<cplx>& M, int m) {
         }
         best = std::min(best, hi);
         if (hi - lo <= 1e-4 * hi || ymax <= 0.0) break;
-        for (int i = 0; i < m; ++i) x[i] = y[i] / ymax + 1e-6;
+        if (shift < 0.0) shift = 0.5 * hi;
+        double zmax = 0.0;
+        for (int i = 0; i < m; ++i) {
+            y[i] += shift * x[i];
+            zmax = std::max(zmax, y[i]);
+        }
+        for (int i = 0; i < m; ++i) x[i] = y[i] / zmax + 1e-6;
     }
     return best;
 }
@@ -585,6 +593,14 @@ int qoc_basis_block_matrices(const qoc_basis* B, int b, double* h0, double* hc) 
     const auto& blk = B->blocks[b];
     if (h0) std::memcpy(h0, blk.h0.data(), blk.h0.size() * sizeof(cplx));
     if (hc) std::memcpy(hc, blk.hc.data(), blk.hc.size() * sizeof(cplx));
+    return QOC_OK;
+}
+
+int qoc_basis_norm_bounds(const qoc_basis* B, int b, double* out) {
+    if (!B || !out || b < 0 || b >= (int)B->blocks.size()) return set_error(QOC_EINVAL, "bad argument");
+    const auto& blk = B->blocks[b];
+    out[0] = blk.h0_norm;
+    for (size_t j = 0; j < blk.hc_norm.size(); ++j) out[1 + j] = blk.hc_norm[j];
     return QOC_OK;
 }
 

@@ -143,3 +143,28 @@ def test_host_first_block_resonances_full_coupling():
 
     assert len(resonances(I.ising_ring(4, 1.0, 0.8, 1.0, 1))) == 3
     assert len(resonances(I.ising_ring_full(4, 1.0, [0.8, 0.37], 1.0, 1))) == 6
+
+
+@pytest.mark.parametrize("system", [I.c1_system(), I.xxz_ring(8, 1.0, 10), I.ising_ring(7, 1.0, 0.6, 1.0, 10),
+                                    I.sn_allpairs(6, 0.7, 0.3, 1.0, 10), I.xxz_ring(10, 0.32, 10)],
+                         ids=["c1", "xxz8", "ising7", "sn6", "xxz10"])
+def test_norm_bounds_enclose_spectral_norms(system):
+    # The per-block bounds that fix the Taylor degree: never below the spectral norm (the truncation
+    # bound stays rigorous), never above the 1-norm (no slice needs more products than with it), and
+    # equal to it where the moduli of a block are the block up to a diagonal sign change (real
+    # blocks with one sign pattern, e.g. the S_n J blocks), where rho(|M|) = rho(M).
+    from paper_2309_05884_gb300 import api
+    B = api.Basis(system)
+    tighter = 0
+    for b, (_, m, _, _) in enumerate(B.blocks):
+        h0, hc = B.block_matrices(b)
+        bounds = B.norm_bounds(b)
+        for M, nb in zip([h0] + list(hc), bounds):
+            two = np.abs(np.linalg.eigvalsh(M)).max() if m > 0 else 0.0
+            one = np.abs(M).sum(axis=0).max()
+            assert two - 1e-12 * max(1.0, one) <= nb <= one * (1 + 1e-12) + 1e-300, (b, two, nb, one)
+            rho_abs = np.abs(np.linalg.eigvals(np.abs(M))).max()
+            assert nb <= rho_abs * (1 + 1e-2) + 1e-12, (b, nb, rho_abs)  # converged to rho(|M|)
+            tighter += nb < one * (1 - 1e-3)
+    if system.n >= 8:
+        assert tighter > 0  # the bound improves on the 1-norm somewhere
