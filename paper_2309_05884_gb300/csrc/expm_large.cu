@@ -78,8 +78,13 @@ struct XlItem {
 
 // Horner steps in Y^2 of each of A(Y), B(Y) after the initial iterate, for degree 2q - 1
 __host__ __device__ __forceinline__ int xl_kst(int q) { return q <= 2 ? 0 : (q % 2 ? (q - 3) / 2 : q / 2 - 1); }
-// coefficient of Y^i in A(Y) (chain 0: c_{2i}) or B(Y) (chain 1: c_{2i+1}); zero past degree 2q - 1
-__device__ __forceinline__ float xl_pc(int chain, int i, int q) { return i < q ? xl_coef[2 * i + chain] : 0.f; }
+// coefficient of Y^i in A(Y) - I (chain 0: c_{2i}, with c_0 = 1 left out) or B(Y) (chain 1: c_{2i+1});
+// zero past degree 2q - 1.  The chain carries A - I, whose entries are small: rounded to FP32 (and
+// to the 22-bit planes) A itself, close to the identity, would add a rounding of 2^-24 per diagonal
+// entry to U on top of U's own; the final product adds I exactly.
+__device__ __forceinline__ float xl_pc(int chain, int i, int q) {
+    return (i < q && (chain != 0 || i != 0)) ? xl_coef[2 * i + chain] : 0.f;
+}
 
 // Scratch of one slice: seven plane sets of pbytes each, all A side (rows of the matrix).
 constexpr int XL_SETS = 7;
@@ -241,12 +246,12 @@ __device__ __forceinline__ void xl_acc8(uint32_t hre, uint32_t him, uint32_t cre
 // Modes of the product kernel (one launch: one product for every participating slice of a chunk):
 //   XL_Y     Y = X X (slices q >= 2); A = rows of X, B = rows of X^T = -conj(X) (the X planes, real
 //            parts negated by the MMA's negate bits); out Y (scale 2^eY) and, for q = 2, the final
-//            A(Y) = c0 I + c2 Y and B(Y) = c1 I + c3 Y (2^eS);
+//            A(Y) - I = c2 Y and B(Y) = c1 I + c3 Y (2^eS);
 //   XL_Y2    Y^2 = Y Y (q >= 3); B = rows of Y^T = conj(Y) (the Y planes, imaginary parts negated);
 //            out Y^2 (2^eY2, if a Horner step follows) and the initial iterates of A(Y) and B(Y);
 //   XL_STEP  Horner step k of chain z = blockIdx.z (0: A, 1: B; slices with k < kst(q)):
 //            T <- p_{2k} I + p_{2k+1} Y + Y^2 T, with B = rows of T^T = conj(T);
-//   XL_FIN   U = A(Y) + X B(Y) (q >= 2) into the propagator store, B = rows of conj(B(Y)).
+//   XL_FIN   U = I + (A(Y) - I) + X B(Y) (q >= 2) into the propagator store, B = rows of conj(B(Y)).
 // Y, Y^2 and every iterate are polynomials in the Hermitian Y, hence Hermitian: those products form
 // the tiles tm <= tn only (grid tiles (tiles + 1) / 2 per slice) and write each off-diagonal tile's
 // conjugate transpose as well.  Y = X X and Y^2 = Y Y keep the (lo, lo) split products (their two
@@ -487,10 +492,13 @@ xl_gemm_kernel(DevPlan P, const XlItem* __restrict__ items, unsigned char* __res
                 float2 v[8];
                 xl_acc8(hre + lb + cl, him + lb + cl, cre + lb + cl, cim + lb + cl, unscale, v);
 #pragma unroll
-                for (int c = 0; c < 8; c += 2)
+                for (int c = 0; c < 8; c += 2) {
+                    const int col = col0 + cl + c;  // + I (the chain holds A - I)
+                    const float d0 = (r == col && r < m) ? 1.f : 0.f, d1 = (r == col + 1 && r < m) ? 1.f : 0.f;
                     *reinterpret_cast<float4*>(&T[lrow * XL_UST + cl + c]) =
-                        make_float4(v[c].x + xv[g][c].x, v[c].y + xv[g][c].y, v[c + 1].x + xv[g][c + 1].x,
+                        make_float4(v[c].x + xv[g][c].x + d0, v[c].y + xv[g][c].y, v[c + 1].x + xv[g][c + 1].x + d1,
                                     v[c + 1].y + xv[g][c + 1].y);
+                }
             }
             __syncthreads();
             float2* Uo = Uout + B.u_off + (size_t)X.kw * B.mmp;
