@@ -495,9 +495,10 @@ def run_ours(args, rank, world):
                          "achieved": expm_flop / (phase_ms["expm"] * 1e-3) / 1e12, "peak": tc_peak,
                          "unit": "TFLOP/s", "peak_source": tc_src,
                          "flops_per_step": expm_flop,
-                         "note": "algorithmic complex-FP32 flop (8 m^3 per product) over the summed durations of "
-                                 "the exponential launches; the split issues 16 real FP16 products per complex "
-                                 "product (12 in the Horner steps, which leave out lo*lo) on padded operands"
+                         "note": "algorithmic complex-FP32 flop (8 m^3 per product; a Hermitian product of the "
+                                 "large-block path, formed on the upper tiles and mirrored, counts as half) over "
+                                 "the summed durations of the exponential launches; the split issues 16 real FP16 "
+                                 "products per complex product (12 where lo*lo is left out) on padded operands"
                                  + ("; checkpointed: every exponential is computed twice (forward pass and "
                                     "costate pass), both counted" if ckpt else "")}
         # a complex product is 4 real products of 4 (or, without lo*lo, 3) split FP16 products each:
